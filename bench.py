@@ -1,0 +1,350 @@
+#!/usr/bin/env python3
+"""Benchmark of the collision-operator hot path on GB300.
+
+One step = one pass of the hot path over one batch: the fused collision kernel
+Q^R(f,f) on 4096 cells (N = 32, hard spheres, M = 48 directions, Mr = 16, FP64)
+followed by the moments / realizability / mask kernel on the same cells.
+Prints ONE JSON line (rank 0).  Default: 1 GPU, --steps 5 --warmup 3.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU runs (torchrun, one rank per GPU) are independent replicas: each rank
+evaluates its own 4096-cell batch (weak scaling, no data-path collective); the
+reported time is the max over ranks.  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(N=32, L=(3.0 + math.sqrt(2.0)) * 3.0, lam=1.0, M=48, Mtheta=4, Mr=16, cells=4096,
+                eta0=1e-3, delta0=1e-4)
+METRIC = "Q(f,f) cell-evals/s at N=32^3 (mixed vs FP64, L2 err); %HBM/tensor peak; p50/p99 ms"
+
+
+def algorithmic_flops_per_cell(N: int, n_terms_gain: int) -> float:
+    """Transforms T = 2 * (gain terms) + 3 real 3D transforms of N^3 points, each
+    2.5 N^3 log2(N^3) flops, plus 4 flops per gain term per point and 3 per
+    point for the loss (the per-cell count of the method)."""
+    T = 2 * n_terms_gain + 3
+    n3 = N ** 3
+    return T * 2.5 * n3 * math.log2(n3) + 4 * n_terms_gain * n3 + 3 * n3
+
+
+def fp64_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
+    """FP64 pipe peak: 2 DFMA per clock per SM (4 flop), the unit count behind
+    GB300's nominal 1.25 TFLOP/s at 2.07 GHz."""
+    return sms * 4 * sm_mhz * 1e6 / 1e12
+
+
+def src_hash() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2505_03360_gb300", "csrc", "*"))):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = sorted(float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit())
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _smi_id(torch, dev, local_rank):
+    """nvidia-smi -i selector of the device torch uses (UUID when available)."""
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        if u:
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        return vis.split(",")[local_rank].strip()
+    return str(local_rank)
+
+
+def load_traffic(kernel_key: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if taken on the current source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        e = d.get(kernel_key)
+        if e and e.get("src_hash") == src_hash():
+            return e.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+    return None
+
+
+def oracle_sample(n_cells: int, seed_offset: int = 0):
+    """Time the CPU oracle (as it stands) on n_cells cells of the workload."""
+    import numpy as np
+    from oracle import moments as om
+    from oracle.collision import q_fast
+    from oracle.kernel import Params, multipliers
+    from paper_2505_03360_gb300 import synth
+    w = WORKLOAD
+    p = Params(N=w["N"], L=w["L"], lam=w["lam"], M=w["M"], Mtheta=w["Mtheta"], Mr=w["Mr"])
+    m = multipliers(p)                                   # plan setup, outside the timing
+    f = synth.bimodal_batch(n_cells, w["N"], w["L"], seed=synth.BASE_SEED + 2 + seed_offset)
+    t0 = time.perf_counter()
+    for c in range(n_cells):
+        q_fast(f[c], p, m)
+        om.cell_moments(f[c], w["L"], w["eta0"], w["delta0"])
+    return time.perf_counter() - t0
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    w = WORKLOAD
+    per_step = 8
+    for _ in range(args.warmup):
+        oracle_sample(1)
+    tt = 0.0
+    for s in range(args.steps):
+        tt += oracle_sample(per_step, seed_offset=s)
+    value = per_step * args.steps / tt
+    line = {"metric": METRIC, "value": value, "unit": "cell-evals/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "4096-cell batch, N=32^3, hard spheres (lambda=1), M=48, Mr=16, FP64 + moments/mask; "
+                                   "each step a %d-cell sample on the host" % per_step,
+                       "global_batch": w["cells"], "seq_len": w["N"] ** 3, "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": "cell-evals/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d cells per step x %d steps of the 4096-cell workload" % (per_step, args.steps)},
+            "e2e": {"value": value, "unit": "cell-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2505_03360_gb300 import coll, synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = WORKLOAD
+    N, n = w["N"], w["cells"]
+    f_host = synth.bimodal_batch(n, N, w["L"], seed=synth.BASE_SEED + 2 + 1000 * rank)
+    f_pin = torch.from_numpy(f_host).pin_memory()
+    f = f_pin.to(dev)
+    del f_host
+    Q = torch.empty_like(f)
+    plan = coll.Plan(N, w["L"], lam=w["lam"], M=w["M"], Mtheta=w["Mtheta"], Mr=w["Mr"], prec="f64",
+                     max_cells=n, device=dev)
+    ws = plan.reserve(n)
+    mom = torch.empty((n, coll.MOMENT_DOUBLES), dtype=torch.float64, device=dev)
+    mask = torch.empty((n,), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        coll.coll_eval_batch(plan.handle, f, Q, n, ws, stream=stream)
+        if ev is not None:
+            ev[1].record(stream)
+        coll.moments_realizability(f, 0, N, w["L"], n, w["eta0"], w["delta0"], mom, mask, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = coll.coll_launch_count()
+    with ClockSampler(_smi_id(torch, dev, local_rank)) as clk:
+        torch.cuda.synchronize(dev)
+        t_start.record(stream)
+        for k in range(args.steps):
+            step(evs[k])
+        t_end.record(stream)
+        torch.cuda.synchronize(dev)
+    launches = coll.coll_launch_count() - launches0
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    coll_ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    assert plan.status() == coll.COLL_OK
+    if world > 1:
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        dist.barrier()
+
+    # end to end through the C ABI from pinned host buffers: H2D f, evaluate, D2H Q + moments + mask
+    Q_pin = torch.empty(Q.shape, dtype=Q.dtype).pin_memory()
+    mom_pin = torch.empty(mom.shape, dtype=mom.dtype).pin_memory()
+    mask_pin = torch.empty(mask.shape, dtype=mask.dtype).pin_memory()
+    e2e_steps = max(2, min(args.steps, 3))
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            f.copy_(f_pin, non_blocking=True)
+            step()
+            Q_pin.copy_(Q, non_blocking=True)
+            mom_pin.copy_(mom, non_blocking=True)
+            mask_pin.copy_(mask, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # FP32 variant on the same cells (reported beside the FP64 line)
+    f32 = f.float()
+    Q32 = torch.empty_like(f32)
+    plan32 = coll.Plan(N, w["L"], lam=w["lam"], M=w["M"], Mtheta=w["Mtheta"], Mr=w["Mr"], prec="f32",
+                       max_cells=n, device=dev)
+    ws32 = plan32.reserve(n)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            coll.coll_eval_batch(plan32.handle, f32, Q32, n, ws32, stream=stream)
+    torch.cuda.synchronize(dev)
+    a32, b32 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a32.record(stream)
+    for _ in range(args.steps):
+        coll.coll_eval_batch(plan32.handle, f32, Q32, n, ws32, stream=stream)
+    b32.record(stream)
+    torch.cuda.synchronize(dev)
+    t32 = a32.elapsed_time(b32) / 1e3 / args.steps
+    err32 = float(torch.linalg.vector_norm(Q32.double() - Q) / torch.linalg.vector_norm(Q))
+
+    if rank != 0:
+        return
+    total_cells = n * world * args.steps
+    value = total_cells / elapsed
+    clocks = clk.summary()
+    n_gain = plan.n_terms - 1
+    flops = algorithmic_flops_per_cell(N, n_gain) * n
+    achieved = flops / (coll_ms / 1e3) / 1e12
+    sm_for_peak = 2070.0
+    peak = fp64_peak_tflops(sm_for_peak)
+    traffic = load_traffic("collision_f64_n32")
+    e2e_bytes_in = f.numel() * 8
+    e2e_bytes_out = Q.numel() * 8 + mom.numel() * 8 + mask.numel()
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "4096-cell batch, N=32^3, hard spheres (lambda=1), M=48 (24 hemisphere directions), "
+                               "Mr=16, FP64 collision + FP64 moments/realizability mask (eta0=1e-3, delta0=1e-4)",
+                   "global_batch": n * world, "seq_len": N ** 3, "parallelism": "replicas x%d" % world,
+                   "l2": "inputs larger than L2 (f and Q are 1.07 GB each)"},
+        "e2e": {"value": n * world * e2e_steps / e2e_s, "unit": "cell-evals/s", "h2d_bytes_per_step": e2e_bytes_in,
+                "d2h_bytes_per_step": e2e_bytes_out},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "collision_kernel<32,double,double>",
+                     "peak_basis": "FP64 pipe, 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived; nominal 1.25 TF)",
+                     "flops_per_launch": flops, "ms_per_launch": coll_ms},
+        "clocks": clocks,
+        "variants": {"f32": {"value": n / t32, "unit": "cell-evals/s", "rel_l2_vs_f64": err32,
+                             "ms_per_launch": 1e3 * t32}},
+    }
+    if not args.no_cpu_baseline:
+        ncell = 48
+        tcpu = oracle_sample(ncell)
+        line["cpu_baseline"] = {"value": ncell / tcpu, "unit": "cell-evals/s", "cores": 1, "kind": "oracle",
+                                "sample": "%d cells of the 4096-cell workload (q_fast + moments, FP64 numpy)" % ncell}
+    print(json.dumps(line), flush=True)
+    plan.close()
+    plan32.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * coll.h -- C ABI of the GB300 collision-operator library (libcoll.so).
+ *
+ * The library evaluates, for a batch of spatial cells, the truncated Carleman
+ * form of the Boltzmann collision operator on a periodic 3D velocity grid
+ * (arxiv 2505.03360, sec. 4.4.1, eq. for Q^R and the separated kernel
+ * beta_F = sum_p alpha_p alpha'_p), and the per-cell moments / realizability
+ * test that decides which cells need it (sec. 3.2, eq. for V_eps; App. A;
+ * sec. 3.3, L1 criterion).
+ *
+ * Conventions shared by every entry point
+ *   - Memory: every data pointer (f, Q, workspace, moments, mask) is a DEVICE
+ *     pointer owned by the caller; the library never frees it.  A plan owns
+ *     only its device tables (allocated in coll_plan_create, freed in
+ *     coll_plan_destroy).  Evaluation calls never allocate.
+ *   - Streams: work is enqueued asynchronously on the given cudaStream_t
+ *     (0 = legacy default stream).  Argument errors are detected on the host
+ *     before anything is launched and returned synchronously.
+ *   - Device-side errors (bounded-wait timeouts, non-finite results) are
+ *     recorded in a sticky status word of the plan, read by
+ *     coll_device_status() after the caller synchronises the stream.
+ *   - The library never calls abort, exit or printf.
+ *   - Threads: a plan is immutable after creation and may be used from
+ *     several host threads / streams concurrently, each with its own
+ *     workspace.
+ *   - Layout: a cell's distribution f is N^3 contiguous values in C order,
+ *     f[j0][j1][j2] = f(v_{j0}, v_{j1}, v_{j2}) with v_j = -L + j * 2L/N
+ *     (velocity grid of sec. 4.1, which contains v = 0).  Cells are
+ *     contiguous: cell c starts at c * N^3 elements.
+ */
+#ifndef COLL_H
+#define COLL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t without pulling in the CUDA headers. */
+typedef struct CUstream_st* coll_stream;
+
+typedef struct coll_plan_s* coll_plan;   /* opaque; immutable after create */
+
+typedef enum {
+  COLL_OK = 0,
+  COLL_EINVAL = 1,        /* invalid argument (null pointer, bad size, ...) */
+  COLL_EUNSUPPORTED = 2,  /* valid but not implemented (e.g. N, precision)  */
+  COLL_ENOMEM = 3,        /* device allocation of plan tables failed /
+                             workspace smaller than coll_workspace_size()    */
+  COLL_ECUDA = 4,         /* a CUDA runtime call failed                      */
+  COLL_ETIMEOUT = 5,      /* a bounded device-side wait gave up              */
+  COLL_ENONFINITE = 6     /* a non-finite value was produced                 */
+} coll_status;
+
+typedef enum {
+  COLL_F64 = 0,           /* transforms and products in FP64                  */
+  COLL_F32 = 1,           /* transforms and products in FP32                  */
+  COLL_MIXED_F16X2 = 2,   /* DFT-GEMM on tensor cores, f16 hi+lo split        */
+  COLL_MIXED_BF16X3 = 3   /* DFT-GEMM on tensor cores, bf16 three-term split  */
+} coll_precision;
+
+/*
+ * Plan descriptor (sec. 4.4.1 "The 3d case", with the readings listed in the
+ * design notes):
+ *   N        points per velocity axis; 16, 24, 32, 48 or 64 (FP64: 16, 24, 32)
+ *   L        half-width of the periodic velocity box [-L, L)^3
+ *   S        support radius; truncation R = 2S (sec. 4.4.1, Q^R);
+ *            0 selects S = 2L / (3 + sqrt 2), the no-overlap bound
+ *   lambda   VHS exponent gamma of B = b0 |g|^gamma (sec. 2.1); 0 <= lambda <= 1
+ *   b0       kernel constant C_gamma; <= 0 selects 1/(4 pi) for lambda = 0
+ *            (int b dsigma = 1, BKW normalisation) and 1 otherwise
+ *   M        number of directions on the full sphere (antipodal pairs share a
+ *            multiplier, so M/2 hemisphere directions are used)
+ *   Mtheta   sphere_rule 0: Gauss-Legendre nodes in cos(theta) (even);
+ *            Mphi = M / Mtheta uniform azimuths (even).
+ *            sphere_rule 1: A1 = Mtheta polar midpoints, A2 = M/(2 A1)
+ *            azimuthal midpoints over a hemisphere (the paper's grid).
+ *   Mr       Gauss-Legendre nodes of the radius |x| on [0, R]
+ *   sphere_rule  0 (default) or 1, see above
+ *   dealias  0: N-point circular products (the only mode implemented on the
+ *            GPU; 1 returns COLL_EUNSUPPORTED)
+ *   prec     compute precision of the transforms (coll_precision)
+ *   io_dtype 0: f and Q are double; 1: f and Q are float
+ */
+typedef struct {
+  int32_t N;
+  double L;
+  double S;
+  double lambda;
+  double b0;
+  int32_t M;
+  int32_t Mtheta;
+  int32_t Mr;
+  int32_t sphere_rule;
+  int32_t dealias;
+  int32_t prec;
+  int32_t io_dtype;
+} coll_plan_desc;
+
+/*
+ * Build a plan: quadrature rules, the multiplier tables alpha_t, alpha'_t and
+ * the loss multiplier Lambda = sum_t c_t alpha_t alpha'_t on the half spectrum
+ * (sec. 4.4.1, eq. beta_F ~ sum_p alpha_p(l) alpha'_p(m)), uploaded once to the
+ * current device.  Returns COLL_EINVAL / COLL_EUNSUPPORTED for bad or
+ * unsupported descriptors, COLL_ENOMEM / COLL_ECUDA if the upload fails; *out
+ * is set only on COLL_OK.
+ */
+coll_status coll_plan_create(const coll_plan_desc* desc, coll_plan* out);
+
+/* Free the plan's device tables.  The caller must ensure no launch using the
+ * plan is still in flight (synchronise its streams first). */
+coll_status coll_plan_destroy(coll_plan plan);
+
+/* Number of separated terms T the plan evaluates per cell, including the loss
+ * term (M/2 for lambda = 1, M/2 * Mr otherwise, plus 1). */
+coll_status coll_plan_terms(coll_plan plan, int32_t* n_terms);
+
+/*
+ * Device workspace (bytes) needed by coll_eval_batch for up to max_cells
+ * cells on the plan's device.  The workspace holds per-CTA scratch of the
+ * persistent kernel (forward spectrum, transposed slabs, gain accumulator);
+ * its size depends on the grid size, not on max_cells beyond the CTA count.
+ */
+coll_status coll_workspace_size(coll_plan plan, int64_t max_cells, size_t* bytes);
+
+/*
+ * Q[c] = Q^R(f[c], f[c]) for c = 0 .. n_cells-1 (sec. 4.4.1):
+ *   fh = DFT(f) with every |k_d| = N/2 mode dropped;
+ *   Q  = sum_t IDFT(c_t alpha_t fh) * IDFT(alpha'_t fh) - IDFT(fh) * IDFT(Lambda fh).
+ * f, Q: device arrays of n_cells * N^3 elements of the plan's io_dtype; Q may
+ * not alias f.  ws: device workspace of at least coll_workspace_size(plan,
+ * n_cells) bytes, 256-byte aligned.  n_cells = 0 is a no-op returning COLL_OK.
+ */
+coll_status coll_eval_batch(coll_plan plan, const void* f, void* Q, int64_t n_cells,
+                            void* ws, size_t ws_bytes, coll_stream stream);
+
+/*
+ * Ragged batch: n_groups groups, each with its own plan (different N and/or
+ * precision), its own f and Q arrays and cells_per_group[g] cells, evaluated
+ * in ONE persistent launch that schedules the largest cells first.  All plans
+ * must live on the current device and share the same precision class
+ * (COLL_F32 or COLL_F64 for every group).  ws must hold at least
+ * coll_ragged_workspace_size() bytes for the same groups.
+ */
+typedef struct {
+  coll_plan plan;
+  const void* f;
+  void* Q;
+} coll_cell_group;
+
+coll_status coll_ragged_workspace_size(const coll_cell_group* groups, const int64_t* cells_per_group,
+                                       int32_t n_groups, size_t* bytes);
+coll_status coll_eval_ragged(const coll_cell_group* groups, const int64_t* cells_per_group,
+                             int32_t n_groups, void* ws, size_t ws_bytes, coll_stream stream);
+
+/*
+ * Per-cell moments record (sec. 2 H3; sec. 2.2 stress tensor; sec. 3.1 Abar,
+ * Bbar; App. A tau, q, Cbar; sec. 3.2 V_eps).  Symmetric 3x3 tensors are
+ * packed xx, yy, zz, xy, xz, yz.  eig are the eigenvalues of V_eps in
+ * ascending order; l1 = ||f - M_{rho,u,T}||_{L1}.  40 doubles.
+ */
+typedef struct {
+  double rho, u[3], T, Theta[6], tau[6], q[3], Abar[6], Bbar[3], Cbar, V[6], eig[3], l1;
+} coll_moments;
+
+/*
+ * Moments, realizability and regime bits for n_cells cells of N^3 values
+ * (io_dtype 0 = double, 1 = float) on the box [-L, L)^3.
+ * mask_out[c] bits:
+ *   bit0  realizability matrix M of sec. 3.2 not PSD (App. A Schur form)
+ *   bit1  Euler breakdown: some eigenvalue lambda of V_eps with |lambda-1| > eta0
+ *   bit2  ||f - M||_L1 > delta0 (sec. 3.3)
+ *   bit7  the cell holds a non-finite value (bits 0-2 set too, moments NaN)
+ * Every grid sum is an exact fixed-point integer sum, so mom_out (except eig)
+ * and mask_out are bitwise reproducible and independent of launch shape.
+ * f, mom_out (n_cells records) and mask_out (n_cells bytes) are device
+ * pointers.  n_cells = 0 is a no-op.
+ */
+coll_status moments_realizability(const void* f, int32_t io_dtype, int32_t N, double L,
+                                  int64_t n_cells, double eta0, double delta0,
+                                  coll_moments* mom_out, uint8_t* mask_out, coll_stream stream);
+
+/* Sticky device status of a plan (COLL_OK, COLL_ETIMEOUT, COLL_ENONFINITE);
+ * synchronous: copies the word from the device.  Reading does not clear it. */
+coll_status coll_device_status(coll_plan plan);
+
+/* Clear the sticky device status of a plan (synchronous). */
+coll_status coll_device_status_clear(coll_plan plan);
+
+/* Static, human-readable name of a status code. */
+const char* coll_status_string(coll_status s);
+
+/* Number of kernels the library launched in this process (all entry points);
+ * a host-side counter for launch accounting. */
+int64_t coll_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COLL_H */

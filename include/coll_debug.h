@@ -1,0 +1,30 @@
+/*
+ * coll_debug.h -- host-only inspection entry point of libcoll.so.
+ *
+ * coll_plan_tables_host builds, on the host and without touching any GPU, the
+ * multiplier tables a plan would upload (sec. 4.4.1, separated kernel
+ * beta_F ~ sum_t alpha_t alpha'_t): n_terms * N * N * (N/2) pairs
+ * (A_t, B_t) = (c_t alpha_t / (s_t N^3), s_t alpha'_t / N^3), the last term
+ * being the loss (-Lambda / (s N^3), s / N^3), where s_t is a power of two
+ * that balances the two factors (A_t B_t does not depend on it); layout
+ * [t][k0][k1][k2 < N/2][2], k0 and k1 in FFT order.  out may be NULL to query *n_terms and *n_doubles only.
+ * Returns COLL_EINVAL / COLL_EUNSUPPORTED like coll_plan_create, and
+ * COLL_ENOMEM if cap (in doubles) is too small.
+ */
+#ifndef COLL_DEBUG_H
+#define COLL_DEBUG_H
+
+#include "coll.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+coll_status coll_plan_tables_host(const coll_plan_desc* desc, double* out, size_t cap, int32_t* n_terms,
+                                  size_t* n_doubles);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COLL_DEBUG_H */

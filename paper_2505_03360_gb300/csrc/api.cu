@@ -1,0 +1,220 @@
+// extern "C" entry points of libcoll.so (declared in include/coll.h).
+// Argument checking on the host, plan tables uploaded once, launches
+// enqueued on the caller's stream.  No entry point aborts or prints.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "coll_internal.h"
+#include "../../include/coll_debug.h"
+
+namespace coll {
+static std::atomic<long long> g_launches{0};
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace coll
+
+using namespace coll;
+
+namespace {
+
+bool valid_N(int N, bool f64) {
+  if (f64) return N == 16 || N == 24 || N == 32;
+  return N == 16 || N == 24 || N == 32 || N == 48 || N == 64;
+}
+
+bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
+
+int grid_for(const coll_plan_s* p, long long n_cells) {
+  long long g = static_cast<long long>(p->num_sms) * p->ctas_per_sm;
+  if (g > n_cells) g = n_cells;
+  if (g < 1) g = 1;
+  return int(g);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* coll_status_string(coll_status s) {
+  switch (s) {
+    case COLL_OK: return "COLL_OK";
+    case COLL_EINVAL: return "COLL_EINVAL: invalid argument";
+    case COLL_EUNSUPPORTED: return "COLL_EUNSUPPORTED: unsupported configuration";
+    case COLL_ENOMEM: return "COLL_ENOMEM: allocation failed or workspace too small";
+    case COLL_ECUDA: return "COLL_ECUDA: CUDA runtime error";
+    case COLL_ETIMEOUT: return "COLL_ETIMEOUT: bounded device wait expired";
+    case COLL_ENONFINITE: return "COLL_ENONFINITE: non-finite value produced";
+  }
+  return "unknown coll_status";
+}
+
+int64_t coll_launch_count(void) { return g_launches.load(); }
+
+coll_status coll_plan_create(const coll_plan_desc* desc, coll_plan* out) {
+  if (!desc || !out) return COLL_EINVAL;
+  const coll_plan_desc d = *desc;
+  if (!(d.L > 0) || !std::isfinite(d.L) || d.S < 0 || !(d.lambda >= 0 && d.lambda <= 1) || d.M <= 0 ||
+      d.Mtheta <= 0 || d.Mr <= 0 || d.Mr > 256 || (d.io_dtype != 0 && d.io_dtype != 1) ||
+      (d.sphere_rule != 0 && d.sphere_rule != 1) || (d.dealias != 0 && d.dealias != 1))
+    return COLL_EINVAL;
+  if (d.prec != COLL_F64 && d.prec != COLL_F32 && d.prec != COLL_MIXED_F16X2 && d.prec != COLL_MIXED_BF16X3)
+    return COLL_EINVAL;
+  if (d.dealias) return COLL_EUNSUPPORTED;
+  if (d.prec == COLL_MIXED_F16X2 || d.prec == COLL_MIXED_BF16X3) return COLL_EUNSUPPORTED;
+  const bool f64 = d.prec == COLL_F64;
+  if (!valid_N(d.N, f64)) return COLL_EUNSUPPORTED;
+
+  HostTables ht;
+  coll_status st = build_tables(d, &ht);
+  if (st != COLL_OK) return st;
+
+  coll_plan_s* p = new (std::nothrow) coll_plan_s();
+  if (!p) return COLL_ENOMEM;
+  p->d = d;
+  p->f64 = f64;
+  p->io_f64 = d.io_dtype == 0;
+  p->n_terms = ht.n_terms;
+  if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return COLL_ECUDA; }
+  cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+  if (!layout_info(d.N, f64, &p->lay)) { delete p; return COLL_EUNSUPPORTED; }
+  int per = 0;
+  if (collision_max_ctas_per_sm(d.N, f64, p->io_f64, &per) != 0 || per < 1) {
+    delete p;
+    return COLL_ECUDA;
+  }
+  p->ctas_per_sm = per;
+
+  const size_t n = ht.tab.size();
+  p->tab_bytes = n * (f64 ? sizeof(double) : sizeof(float));
+  if (cudaMalloc(&p->tab_dev, p->tab_bytes) != cudaSuccess) { delete p; return COLL_ENOMEM; }
+  cudaError_t e;
+  if (f64) {
+    e = cudaMemcpy(p->tab_dev, ht.tab.data(), p->tab_bytes, cudaMemcpyHostToDevice);
+  } else {
+    std::vector<float> tf(n);
+    for (size_t i = 0; i < n; ++i) tf[i] = float(ht.tab[i]);
+    e = cudaMemcpy(p->tab_dev, tf.data(), p->tab_bytes, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->status_dev), sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->status_dev, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaFree(p->tab_dev);
+    delete p;
+    return COLL_ECUDA;
+  }
+  *out = p;
+  return COLL_OK;
+}
+
+coll_status coll_plan_tables_host(const coll_plan_desc* desc, double* out, size_t cap, int32_t* n_terms,
+                                  size_t* n_doubles) {
+  if (!desc || !n_terms || !n_doubles) return COLL_EINVAL;
+  const coll_plan_desc d = *desc;
+  if (!(d.L > 0) || d.M <= 0 || d.Mtheta <= 0 || d.Mr <= 0 || d.N < 4 || d.N % 2) return COLL_EINVAL;
+  HostTables ht;
+  const coll_status st = build_tables(d, &ht);
+  if (st != COLL_OK) return st;
+  *n_terms = ht.n_terms;
+  *n_doubles = ht.tab.size();
+  if (!out) return COLL_OK;
+  if (cap < ht.tab.size()) return COLL_ENOMEM;
+  std::memcpy(out, ht.tab.data(), ht.tab.size() * sizeof(double));
+  return COLL_OK;
+}
+
+coll_status coll_plan_destroy(coll_plan p) {
+  if (!p) return COLL_EINVAL;
+  cudaFree(p->tab_dev);
+  cudaFree(p->status_dev);
+  delete p;
+  return COLL_OK;
+}
+
+coll_status coll_plan_terms(coll_plan p, int32_t* n_terms) {
+  if (!p || !n_terms) return COLL_EINVAL;
+  *n_terms = p->n_terms;
+  return COLL_OK;
+}
+
+coll_status coll_workspace_size(coll_plan p, int64_t max_cells, size_t* bytes) {
+  if (!p || !bytes || max_cells < 0) return COLL_EINVAL;
+  const long long g = max_cells == 0 ? 0 : grid_for(p, max_cells);
+  *bytes = size_t(g) * p->lay.ws_bytes_per_cta();
+  return COLL_OK;
+}
+
+coll_status coll_eval_batch(coll_plan p, const void* f, void* Q, int64_t n_cells, void* ws, size_t ws_bytes,
+                            coll_stream stream) {
+  if (!p || n_cells < 0) return COLL_EINVAL;
+  if (n_cells == 0) return COLL_OK;
+  if (!f || !Q || f == Q) return COLL_EINVAL;
+  const int grid = grid_for(p, n_cells);
+  const size_t need = size_t(grid) * p->lay.ws_bytes_per_cta();
+  if (need > 0 && (!ws || !aligned256(ws))) return COLL_EINVAL;
+  if (ws_bytes < need) return COLL_ENOMEM;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return COLL_EINVAL;
+  CollArgs a;
+  a.f = f;
+  a.Q = Q;
+  a.n_cells = n_cells;
+  a.tab = p->tab_dev;
+  a.n_terms = p->n_terms;
+  a.ws = ws;
+  a.ws_per_cta = p->lay.ws_bytes_per_cta();
+  a.status = p->status_dev;
+  const int e = launch_collision(p->d.N, p->f64, p->io_f64, a, grid, stream);
+  return e == 0 ? COLL_OK : COLL_ECUDA;
+}
+
+coll_status moments_realizability(const void* f, int32_t io_dtype, int32_t N, double L, int64_t n_cells,
+                                  double eta0, double delta0, coll_moments* mom_out, uint8_t* mask_out,
+                                  coll_stream stream) {
+  if (n_cells < 0 || (io_dtype != 0 && io_dtype != 1) || !(L > 0) || !std::isfinite(L)) return COLL_EINVAL;
+  if (!(N >= 2 && N <= 64 && N % 2 == 0)) return COLL_EINVAL;
+  if (!(eta0 >= 0) || !(delta0 >= 0)) return COLL_EINVAL;
+  if (n_cells == 0) return COLL_OK;
+  if (!f || !mom_out || !mask_out) return COLL_EINVAL;
+  const int e = launch_moments(f, io_dtype == 0, N, L, n_cells, eta0, delta0, mom_out, mask_out, stream);
+  return e == 0 ? COLL_OK : COLL_ECUDA;
+}
+
+coll_status coll_device_status(coll_plan p) {
+  if (!p) return COLL_EINVAL;
+  int v = 0;
+  if (cudaMemcpy(&v, p->status_dev, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return COLL_ECUDA;
+  if (v & kStatusTimeout) return COLL_ETIMEOUT;
+  if (v & kStatusNonFinite) return COLL_ENONFINITE;
+  return COLL_OK;
+}
+
+coll_status coll_device_status_clear(coll_plan p) {
+  if (!p) return COLL_EINVAL;
+  return cudaMemset(p->status_dev, 0, sizeof(int)) == cudaSuccess ? COLL_OK : COLL_ECUDA;
+}
+
+coll_status coll_ragged_workspace_size(const coll_cell_group* groups, const int64_t* cells_per_group,
+                                       int32_t n_groups, size_t* bytes) {
+  (void)groups;
+  (void)cells_per_group;
+  (void)n_groups;
+  (void)bytes;
+  return COLL_EUNSUPPORTED;
+}
+
+coll_status coll_eval_ragged(const coll_cell_group* groups, const int64_t* cells_per_group, int32_t n_groups,
+                             void* ws, size_t ws_bytes, coll_stream stream) {
+  (void)groups;
+  (void)cells_per_group;
+  (void)n_groups;
+  (void)ws;
+  (void)ws_bytes;
+  (void)stream;
+  return COLL_EUNSUPPORTED;
+}
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// Internal declarations shared by the host API (api.cu, plan.cpp) and the
+// CUDA kernels.  Not part of the public ABI (see include/coll.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/coll.h"
+
+namespace coll {
+
+// ---------------------------------------------------------------------------
+// Compile-time layout of the fused collision kernel for (N, precision).
+//
+// Per cell the kernel holds three arrays:
+//   Fh  forward half spectrum, [k0][k1][k2 < N/2] complex, rows padded to N/2+1
+//   W   one v0-slab of the per-term spectrum after the axis-0 inverse pass,
+//       [v0 / S0][k1][k2 < N] complex, rows padded to N+1 (bank-conflict free
+//       row reads in the last pass); slab s holds the planes v0 = s mod S0
+//   G   gain accumulator, N^3 reals
+// Each array lives in shared memory when it fits (227 KB per CTA) and
+// otherwise in the CTA's slice of the global workspace (L2 resident for the
+// sizes used).  S0 splits the axis-0 inverse transform by decimation in
+// frequency so that a slab of W fits on chip.
+// ---------------------------------------------------------------------------
+struct LayoutInfo {
+  int N, S0;
+  bool w_smem, fh_smem, g_smem;
+  int threads;
+  size_t w_bytes, fh_bytes, g_bytes;
+  size_t smem_bytes() const {
+    return (w_smem ? w_bytes : 0) + (fh_smem ? fh_bytes : 0) + (g_smem ? g_bytes : 0);
+  }
+  size_t ws_bytes_per_cta() const {
+    size_t b = (w_smem ? 0 : w_bytes) + (fh_smem ? 0 : fh_bytes) + (g_smem ? 0 : g_bytes);
+    return (b + 255) / 256 * 256;
+  }
+};
+
+// Returns false if (N, is_f64) has no kernel instantiation.
+bool layout_info(int N, bool is_f64, LayoutInfo* out);
+
+struct CollArgs {
+  const void* f;
+  void* Q;
+  long long n_cells;
+  const void* tab;          // [n_terms][N][N][N/2] pairs (A, B) of the compute type
+  int n_terms;
+  void* ws;
+  size_t ws_per_cta;
+  int* status;              // sticky device status bits
+};
+
+// status bits written by kernels
+enum : int { kStatusNonFinite = 1, kStatusTimeout = 2 };
+
+// Launchers (collision.cu); return cudaError_t as int.
+int launch_collision(int N, bool f64, bool io_f64, const CollArgs& a, int grid, void* stream);
+int collision_max_ctas_per_sm(int N, bool f64, bool io_f64, int* ctas);
+
+// Ragged launch: one persistent kernel over mixed N (collision.cu).
+struct RaggedItem {            // one group of cells with the same plan
+  const void* f;
+  void* Q;
+  const void* tab;
+  long long n_cells;
+  long long first_unit;       // prefix sum of n_cells in schedule order
+  int N;
+  int n_terms;
+  int io_f64;
+  int* status;
+};
+int launch_ragged(bool f64, const RaggedItem* items_dev, int n_items, long long total_cells,
+                  void* ws, size_t ws_per_cta, int* counter_dev, int grid, void* stream);
+int ragged_layout(bool f64, size_t* smem_bytes, size_t* ws_per_cta, int* threads);
+int ragged_max_ctas_per_sm(bool f64, int* ctas);
+
+// Moments kernel (moments.cu)
+int launch_moments(const void* f, int io_f64, int N, double L, long long n_cells, double eta0,
+                   double delta0, coll_moments* mom, uint8_t* mask, void* stream);
+
+// Host-side plan building (plan.cpp)
+struct HostTables {
+  int n_terms;
+  std::vector<double> tab;    // [n_terms][N][N][N/2][2]
+};
+coll_status build_tables(const coll_plan_desc& d, HostTables* out);
+
+void count_launches(long long n);
+
+}  // namespace coll
+
+struct coll_plan_s {
+  coll_plan_desc d;
+  int device;
+  int n_terms;
+  bool f64;          // compute precision FP64
+  bool io_f64;       // f / Q element type
+  void* tab_dev;     // device tables in the compute type
+  size_t tab_bytes;
+  int* status_dev;   // sticky status word
+  coll::LayoutInfo lay;
+  int ctas_per_sm;
+  int num_sms;
+};

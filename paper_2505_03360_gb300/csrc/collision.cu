@@ -1,0 +1,94 @@
+// Dispatch of the fused collision kernel over (N, compute type, io type).
+// The kernels themselves are instantiated in coll_inst_*.cu (one translation
+// unit per (N, compute type) so that they compile in parallel).
+#include <cuda_runtime.h>
+
+#include "coll_internal.h"
+#include "collision_layout.cuh"
+
+namespace coll {
+
+template <int N, typename T, typename Tio> int launch_one(const CollArgs& a, int grid, cudaStream_t st);
+template <int N, typename T, typename Tio> int occupancy_one(int* ctas);
+
+template <int N, typename T> LayoutInfo make_info() {
+  using Ly = Lay<N, T>;
+  LayoutInfo i;
+  i.N = N;
+  i.S0 = Ly::S0;
+  i.w_smem = Cfg<N, T>::W;
+  i.fh_smem = Cfg<N, T>::FH;
+  i.g_smem = Cfg<N, T>::G;
+  i.threads = kThreads;
+  i.w_bytes = Ly::round16(Ly::W_BYTES);
+  i.fh_bytes = Ly::round16(Ly::FH_BYTES);
+  i.g_bytes = Ly::round16(Ly::G_BYTES);
+  return i;
+}
+
+bool layout_info(int N, bool f64, LayoutInfo* out) {
+  if (f64) {
+    switch (N) {
+      case 16: *out = make_info<16, double>(); return true;
+      case 24: *out = make_info<24, double>(); return true;
+      case 32: *out = make_info<32, double>(); return true;
+      default: return false;
+    }
+  }
+  switch (N) {
+    case 16: *out = make_info<16, float>(); return true;
+    case 24: *out = make_info<24, float>(); return true;
+    case 32: *out = make_info<32, float>(); return true;
+    case 48: *out = make_info<48, float>(); return true;
+    case 64: *out = make_info<64, float>(); return true;
+    default: return false;
+  }
+}
+
+#define COLL_DISPATCH(FN, ...)                                                              \
+  if (f64) {                                                                                \
+    if (io_f64) {                                                                           \
+      switch (N) {                                                                          \
+        case 16: return FN<16, double, double>(__VA_ARGS__);                                \
+        case 24: return FN<24, double, double>(__VA_ARGS__);                                \
+        case 32: return FN<32, double, double>(__VA_ARGS__);                                \
+      }                                                                                     \
+    } else {                                                                                \
+      switch (N) {                                                                          \
+        case 16: return FN<16, double, float>(__VA_ARGS__);                                 \
+        case 24: return FN<24, double, float>(__VA_ARGS__);                                 \
+        case 32: return FN<32, double, float>(__VA_ARGS__);                                 \
+      }                                                                                     \
+    }                                                                                       \
+  } else {                                                                                  \
+    if (io_f64) {                                                                           \
+      switch (N) {                                                                          \
+        case 16: return FN<16, float, double>(__VA_ARGS__);                                 \
+        case 24: return FN<24, float, double>(__VA_ARGS__);                                 \
+        case 32: return FN<32, float, double>(__VA_ARGS__);                                 \
+        case 48: return FN<48, float, double>(__VA_ARGS__);                                 \
+        case 64: return FN<64, float, double>(__VA_ARGS__);                                 \
+      }                                                                                     \
+    } else {                                                                                \
+      switch (N) {                                                                          \
+        case 16: return FN<16, float, float>(__VA_ARGS__);                                  \
+        case 24: return FN<24, float, float>(__VA_ARGS__);                                  \
+        case 32: return FN<32, float, float>(__VA_ARGS__);                                  \
+        case 48: return FN<48, float, float>(__VA_ARGS__);                                  \
+        case 64: return FN<64, float, float>(__VA_ARGS__);                                  \
+      }                                                                                     \
+    }                                                                                       \
+  }                                                                                         \
+  return int(cudaErrorInvalidValue);
+
+int launch_collision(int N, bool f64, bool io_f64, const CollArgs& a, int grid, void* stream) {
+  count_launches(1);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  COLL_DISPATCH(launch_one, a, grid, st)
+}
+
+int collision_max_ctas_per_sm(int N, bool f64, bool io_f64, int* ctas) {
+  COLL_DISPATCH(occupancy_one, ctas)
+}
+
+}  // namespace coll

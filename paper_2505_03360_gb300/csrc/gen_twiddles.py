@@ -1,0 +1,34 @@
+"""Writes twiddles.h: cos and sin of 2 pi n / 192, n = 0..191, correctly rounded.
+
+192 = lcm(16, 24, 32, 48, 64), so every twiddle of the supported FFT lengths
+and of their radix-2/3/4 sub-lengths is an entry of this table.  Values are
+computed with mpmath at 50 digits and rounded once to double (and from the
+exact value once to float).  Run by hand; the output header is committed.
+"""
+import os
+
+import mpmath
+import numpy as np
+
+mpmath.mp.dps = 50
+rows_d, rows_f = [], []
+for n in range(192):
+    a = 2 * mpmath.pi * n / 192
+    c, s = mpmath.cos(a), mpmath.sin(a)
+    cd, sd = float(c), float(s)
+    cf = float(np.float32(mpmath.nstr(c, 40)))
+    sf = float(np.float32(mpmath.nstr(s, 40)))
+    rows_d.append((cd.hex(), sd.hex()))
+    rows_f.append((cf.hex(), sf.hex()))
+out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "twiddles.h")
+with open(out, "w") as fh:
+    fh.write("// Generated by gen_twiddles.py: cos/sin(2 pi n / 192), correctly rounded.\n")
+    fh.write("#pragma once\n\n")
+    fh.write("static __constant__ double kTwCosD[192] = {\n")
+    fh.write(",\n".join("  %s" % c for c, _ in rows_d) + "};\n")
+    fh.write("static __constant__ double kTwSinD[192] = {\n")
+    fh.write(",\n".join("  %s" % s for _, s in rows_d) + "};\n")
+    fh.write("static __constant__ float kTwCosF[192] = {\n")
+    fh.write(",\n".join("  %sf" % c for c, _ in rows_f) + "};\n")
+    fh.write("static __constant__ float kTwSinF[192] = {\n")
+    fh.write(",\n".join("  %sf" % s for _, s in rows_f) + "};\n")

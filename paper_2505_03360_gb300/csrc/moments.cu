@@ -1,0 +1,517 @@
+// Per-cell moments, realizability matrices, L1 distance and regime bits
+// (arxiv 2505.03360: sec. 2 hypothesis H3 for rho, u, T; sec. 2.2 stress
+// tensor; sec. 3.1 eq. for Abar, Bbar; sec. 3.2 eq. for V_eps; App. A for tau,
+// q, Cbar and the general-Cbar Schur form; sec. 3.3 L1 criterion).
+//
+// Reproducibility: every grid sum is an exact integer.  f is converted to
+// fixed point F = rint(f 2^P) with a per-cell scale P = 61 - e (max|f| < 2^e),
+// multiplied by integer grid monomials (v = dv k, k_d = j_d - N/2) and summed
+// in 128-bit integers, so the result does not depend on the order of the
+// reduction or on the launch shape.  Each sum is rounded once to double, and
+// the scalar algebra is a fixed sequence of correctly rounded double
+// operations without contraction (__dadd_rn / __dmul_rn / __ddiv_rn /
+// __dsqrt_rn).  The Maxwellian of the L1 test is separable; its 1D factors use
+// our own exp (Cody-Waite reduction by ln 2, degree-13 Horner Taylor
+// polynomial) and are rounded to 52-bit fixed point, so |F2 - M_fix| is again
+// an exact integer sum.  Only the eigenvalues of V_eps (closed-form
+// trigonometric solution) are not bit-reproducible.
+//
+// Work per cell: one CTA.  Pass 0 takes max|f|; pass 1 walks rows (j0, j1)
+// and forms the five row sums sum_j2 F k2^c with 32x32->64-bit multiply-adds on
+// a 31-bit split of F, then folds them into the 14 global sums with the row's
+// k0, k1 weights; pass 2 (re-read from L2) accumulates |F2 - M_fix|.
+#include <cuda_runtime.h>
+
+#include "coll_internal.h"
+
+namespace coll {
+
+namespace {
+
+constexpr int kMThreads = 256;
+constexpr int kFixTop = 61;
+constexpr int kEBits = 52;
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
+
+// rint(x * 2^P) (round half to even) for a finite double, exact integer
+// arithmetic on the bit pattern.  The caller guarantees |x| 2^P < 2^62.
+__device__ __forceinline__ long long fix_bits(unsigned long long m, int ex_field, int bias_shift, int P,
+                                              bool neg) {
+  // value = m * 2^(ex_field - bias_shift)
+  const int sh = ex_field - bias_shift + P;
+  unsigned long long r;
+  if (sh >= 0) {
+    r = m << sh;
+  } else if (sh < -60) {
+    r = 0;
+  } else {
+    const int k = -sh;
+    const unsigned long long q = m >> k;
+    const unsigned long long rem = m & ((1ull << k) - 1ull);
+    const unsigned long long half = 1ull << (k - 1);
+    r = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+  }
+  return neg ? -static_cast<long long>(r) : static_cast<long long>(r);
+}
+
+__device__ __forceinline__ long long fix_val(double x, int P) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  int ex = int((b >> 52) & 0x7ffull);
+  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  if (ex == 0) ex = 1; else m |= (1ull << 52);
+  return fix_bits(m, ex, 1075, P, (b >> 63) != 0);
+}
+
+__device__ __forceinline__ long long fix_val(float x, int P) {
+  const unsigned int b = __float_as_uint(x);
+  int ex = int((b >> 23) & 0xffu);
+  unsigned long long m = b & 0x7fffffu;
+  if (ex == 0) ex = 1; else m |= (1ull << 23);
+  return fix_bits(m, ex, 150, P, (b >> 31) != 0);
+}
+
+__device__ __forceinline__ double absval(double x) { return fabs(x); }
+__device__ __forceinline__ float absval(float x) { return fabsf(x); }
+__device__ __forceinline__ bool finite_val(double x) { return isfinite(x); }
+__device__ __forceinline__ bool finite_val(float x) { return isfinite(x); }
+
+// correctly rounded (half to even) conversion of a 128-bit integer to double
+__device__ double i128_to_double(i128 x) {
+  const bool neg = x < 0;
+  u128 u = neg ? static_cast<u128>(-x) : static_cast<u128>(x);
+  if (u == 0) return 0.0;
+  const unsigned long long hi = static_cast<unsigned long long>(u >> 64);
+  const unsigned long long lo = static_cast<unsigned long long>(u);
+  const int nbits = hi ? 128 - __clzll(static_cast<long long>(hi)) : 64 - __clzll(static_cast<long long>(lo));
+  double d;
+  if (nbits <= 53) {
+    d = static_cast<double>(lo);
+  } else {
+    int sh = nbits - 53;
+    u128 q = u >> sh;
+    const u128 rem = u - (q << sh);
+    const u128 half = static_cast<u128>(1) << (sh - 1);
+    if (rem > half || (rem == half && (q & 1))) {
+      q += 1;
+      if (q >> 53) { q >>= 1; sh += 1; }
+    }
+    d = ldexp(static_cast<double>(static_cast<unsigned long long>(q)), sh);
+  }
+  return neg ? -d : d;
+}
+
+// exp(x), x <= 0 (Cody & Waite range reduction by ln 2, Taylor-Horner degree
+// 13, no fused multiply-add).  ln 2 = LN2_HI + LN2_LO with a 32-bit head so
+// that k * LN2_HI is exact; 1/k! rounded once to double.
+__device__ double own_exp(double x) {
+  if (x < -700.0) return 0.0;
+  const double kInvLn2 = 0x1.71547652b82fep+0;
+  const double kLn2Hi = 0x1.62e42ff0p-1;
+  const double kLn2Lo = -0x1.718432a1b0e26p-35;
+  const double c[14] = {1.0,
+                        1.0,
+                        1.0 / 2.0,
+                        1.0 / 6.0,
+                        1.0 / 24.0,
+                        1.0 / 120.0,
+                        1.0 / 720.0,
+                        1.0 / 5040.0,
+                        1.0 / 40320.0,
+                        1.0 / 362880.0,
+                        1.0 / 3628800.0,
+                        1.0 / 39916800.0,
+                        1.0 / 479001600.0,
+                        1.0 / 6227020800.0};
+  const double k = rint(dmul(x, kInvLn2));
+  const double t1 = dmul(k, kLn2Hi);
+  const double t2 = dsub(x, t1);
+  const double t3 = dmul(k, kLn2Lo);
+  const double r = dsub(t2, t3);
+  double p = c[13];
+#pragma unroll
+  for (int n = 12; n >= 0; --n) {
+    p = dmul(p, r);
+    p = dadd(p, c[n]);
+  }
+  const long long ki = static_cast<long long>(k);
+  const double scale = __longlong_as_double((ki + 1023) << 52);   // k >= -1010 here
+  return dmul(p, scale);
+}
+
+__device__ __forceinline__ bool psd3(const double* S) {
+  const double a = S[0], b = S[1], c = S[2], d = S[3], e = S[4], f = S[5];
+  if (!(a >= 0.0 && b >= 0.0 && c >= 0.0)) return false;
+  const double m01 = dsub(dmul(a, b), dmul(d, d));
+  const double m02 = dsub(dmul(a, c), dmul(e, e));
+  const double m12 = dsub(dmul(b, c), dmul(f, f));
+  if (!(m01 >= 0.0 && m02 >= 0.0 && m12 >= 0.0)) return false;
+  // det = (a (bc - f^2) - d (dc - fe)) + e (df - be)
+  const double det = dadd(dsub(dmul(a, m12), dmul(d, dsub(dmul(d, c), dmul(f, e)))),
+                          dmul(e, dsub(dmul(d, f), dmul(b, e))));
+  return det >= 0.0;
+}
+
+// eigenvalues of a symmetric 3x3 matrix, ascending (trigonometric closed form)
+__device__ void eig3(const double* S, double* ev) {
+  const double a = S[0], b = S[1], c = S[2], d = S[3], e = S[4], f = S[5];
+  const double p1 = d * d + e * e + f * f;
+  const double q = (a + b + c) / 3.0;
+  if (p1 == 0.0) {
+    double x = a, y = b, z = c, t;
+    if (x > y) { t = x; x = y; y = t; }
+    if (y > z) { t = y; y = z; z = t; }
+    if (x > y) { t = x; x = y; y = t; }
+    ev[0] = x; ev[1] = y; ev[2] = z;
+    return;
+  }
+  const double p2 = (a - q) * (a - q) + (b - q) * (b - q) + (c - q) * (c - q) + 2.0 * p1;
+  const double p = sqrt(p2 / 6.0);
+  const double B0 = (a - q) / p, B1 = (b - q) / p, B2 = (c - q) / p, B3 = d / p, B4 = e / p, B5 = f / p;
+  const double detB = B0 * (B1 * B2 - B5 * B5) - B3 * (B3 * B2 - B5 * B4) + B4 * (B3 * B5 - B1 * B4);
+  double r = detB / 2.0;
+  r = r < -1.0 ? -1.0 : (r > 1.0 ? 1.0 : r);
+  const double phi = acos(r) / 3.0;
+  const double e1 = q + 2.0 * p * cos(phi);
+  const double e3 = q + 2.0 * p * cos(phi + 2.0943951023931954923);
+  const double e2 = 3.0 * q - e1 - e3;
+  ev[0] = e3; ev[1] = e2; ev[2] = e1;
+}
+
+__device__ __forceinline__ i128 warp_sum(i128 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long lo = static_cast<unsigned long long>(v);
+    const long long hi = static_cast<long long>(v >> 64);
+    const unsigned long long olo = __shfl_down_sync(0xffffffffu, lo, o);
+    const long long ohi = __shfl_down_sync(0xffffffffu, hi, o);
+    const u128 other = (static_cast<u128>(static_cast<unsigned long long>(ohi)) << 64) | static_cast<u128>(olo);
+    v = static_cast<i128>(static_cast<u128>(v) + other);
+  }
+  return v;
+}
+
+// block-wide exact sum of K 128-bit values; result valid in thread 0
+template <int K>
+__device__ void block_sum(i128* v, i128* sred) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < K; ++i) v[i] = warp_sum(v[i]);
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) sred[warp * K + i] = v[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      i128 s = 0;
+      for (int w = 0; w < kMThreads / 32; ++w) s += sred[w * K + i];
+      v[i] = s;
+    }
+  }
+  __syncthreads();
+}
+
+struct CellShared {
+  i128 red[(kMThreads / 32) * 14];
+  double e[3][64];
+  unsigned long long E2[64];
+  double bc[8];          // broadcast: CM, P2, valid flag ...
+  int ibc[4];
+  float fmax_f;
+  unsigned int anybad;
+  double fmax_d;
+};
+
+template <typename Tio>
+__device__ void moments_cell(const Tio* __restrict__ f, int N, double L, double eta0, double delta0,
+                             coll_moments* mom, uint8_t* mask, CellShared& sh) {
+  const int tid = threadIdx.x;
+  const int n3 = N * N * N;
+  const int half = N / 2;
+
+  // ---- pass 0: max |f| and finiteness
+  double mx = 0.0;
+  bool bad = false;
+  for (int i = tid; i < n3; i += kMThreads) {
+    const Tio x = f[i];
+    bad |= !finite_val(x);
+    const double ax = double(absval(x));
+    mx = ax > mx ? ax : mx;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  if (tid == 0) { sh.fmax_d = 0.0; sh.anybad = 0u; }
+  __syncthreads();
+  if ((tid & 31) == 0) {
+    atomicMax(reinterpret_cast<unsigned long long*>(&sh.fmax_d),
+              static_cast<unsigned long long>(__double_as_longlong(mx)));   // mx >= 0: bits order like values
+  }
+  if (bad) atomicOr(&sh.anybad, 1u);
+  __syncthreads();
+  const double fmaxv = sh.fmax_d;
+  const bool invalid = sh.anybad != 0u;
+  double* out = reinterpret_cast<double*>(mom);
+  const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+  if (invalid || fmaxv == 0.0) {
+    if (tid < 40) out[tid] = (tid == 0 && !invalid) ? 0.0 : qnan;
+    if (tid == 0) *mask = invalid ? 0x87 : 0x07;
+    __syncthreads();
+    return;
+  }
+  int ef;
+  frexp(fmaxv, &ef);
+  const int P1 = kFixTop - ef;
+
+  // ---- pass 1: exact integer moment sums
+  i128 acc[14];
+#pragma unroll
+  for (int i = 0; i < 14; ++i) acc[i] = 0;
+  for (int row = tid; row < N * N; row += kMThreads) {
+    const int j0 = row / N, j1 = row % N;
+    const long long k0 = j0 - half, k1 = j1 - half;
+    long long rl[5] = {0, 0, 0, 0, 0}, rh[5] = {0, 0, 0, 0, 0};
+    const Tio* fr = f + size_t(row) * N;
+    for (int j2 = 0; j2 < N; ++j2) {
+      const long long F = fix_val(fr[j2], P1);
+      const int flo = int(F & 0x7fffffffll);
+      const int fhi = int(F >> 31);
+      const int k2 = j2 - half;
+      int kp = 1;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        rl[c] += static_cast<long long>(flo) * kp;
+        rh[c] += static_cast<long long>(fhi) * kp;
+        kp *= k2;
+      }
+    }
+    i128 R[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) R[c] = static_cast<i128>(rh[c]) * (static_cast<i128>(1) << 31) + static_cast<i128>(rl[c]);
+    const long long r2 = k0 * k0 + k1 * k1;
+    acc[0] += R[0];
+    acc[1] += R[0] * k0;
+    acc[2] += R[0] * k1;
+    acc[3] += R[1];
+    acc[4] += R[0] * (k0 * k0);
+    acc[5] += R[0] * (k1 * k1);
+    acc[6] += R[2];
+    acc[7] += R[0] * (k0 * k1);
+    acc[8] += R[1] * k0;
+    acc[9] += R[1] * k1;
+    acc[10] += R[0] * (k0 * r2) + R[2] * k0;
+    acc[11] += R[0] * (k1 * r2) + R[2] * k1;
+    acc[12] += R[1] * r2 + R[3];
+    acc[13] += R[0] * (r2 * r2) + R[2] * (2 * r2) + R[4];
+  }
+  block_sum<14>(acc, sh.red);
+
+  // ---- scalar algebra (thread 0), identical op sequence to the oracle
+  if (tid == 0) {
+    double o[40];
+    for (int i = 0; i < 40; ++i) o[i] = qnan;
+    uint8_t mbits = 0;
+    const double h = ddiv(dmul(2.0, L), double(N));
+    const double vol = dmul(dmul(h, h), h);
+    const double D0 = i128_to_double(acc[0]);
+    const double rho = dmul(ldexp(D0, -P1), vol);
+    o[0] = rho;
+    sh.ibc[0] = 0;
+    if (!(D0 > 0.0)) {
+      mbits = 0x07;
+    } else {
+      const double inv0 = ddiv(1.0, D0);
+      double kap[3], u[3];
+      for (int d = 0; d < 3; ++d) {
+        kap[d] = dmul(i128_to_double(acc[1 + d]), inv0);
+        u[d] = dmul(kap[d], h);
+        o[1 + d] = u[d];
+      }
+      double m2[6];
+      const int pd[6] = {0, 1, 2, 0, 0, 1}, pe[6] = {0, 1, 2, 1, 2, 2};
+      for (int i = 0; i < 6; ++i) m2[i] = dmul(i128_to_double(acc[4 + i]), inv0);
+      double C[6];
+      for (int i = 0; i < 6; ++i) C[i] = dsub(m2[i], dmul(kap[pd[i]], kap[pe[i]]));
+      const double trC = dadd(dadd(C[0], C[1]), C[2]);
+      const double Tg = ddiv(trC, 3.0);
+      const double h2 = dmul(h, h);
+      const double T = dmul(Tg, h2);
+      o[4] = T;
+      if (!(Tg > 0.0)) {
+        mbits = 0x07;
+      } else {
+        double Theta[6], tau[6];
+        for (int i = 0; i < 6; ++i) Theta[i] = dmul(C[i], h2);
+        const double p = dmul(rho, T);
+        for (int i = 0; i < 6; ++i) tau[i] = i < 3 ? dsub(dmul(rho, Theta[i]), p) : dmul(rho, Theta[i]);
+        double E3[3];
+        for (int d = 0; d < 3; ++d) E3[d] = dmul(i128_to_double(acc[10 + d]), inv0);
+        const double kk = dadd(dadd(dmul(kap[0], kap[0]), dmul(kap[1], kap[1])), dmul(kap[2], kap[2]));
+        // symmetric access C(d, e)
+        auto Cs = [&](int d, int e) -> double {
+          if (d == e) return C[d];
+          const int lo = d < e ? d : e, hi = d < e ? e : d;
+          return lo == 0 ? (hi == 1 ? C[3] : C[4]) : C[5];
+        };
+        double m3[3], q[3];
+        const double rv = dmul(rho, vol);
+        for (int d = 0; d < 3; ++d) {
+          const double sC = dadd(dadd(dmul(kap[0], Cs(d, 0)), dmul(kap[1], Cs(d, 1))), dmul(kap[2], Cs(d, 2)));
+          m3[d] = dsub(dsub(dsub(E3[d], dmul(2.0, sC)), dmul(kap[d], trC)), dmul(kap[d], kk));
+          q[d] = dmul(0.5, dmul(rv, m3[d]));
+        }
+        const double E4 = dmul(i128_to_double(acc[13]), inv0);
+        const double kE3 = dadd(dadd(dmul(kap[0], E3[0]), dmul(kap[1], E3[1])), dmul(kap[2], E3[2]));
+        const double trm2 = dadd(dadd(m2[0], m2[1]), m2[2]);
+        const double km2k =
+            dadd(dadd(dadd(dmul(dmul(kap[0], kap[0]), m2[0]), dmul(dmul(kap[1], kap[1]), m2[1])),
+                      dmul(dmul(kap[2], kap[2]), m2[2])),
+                 dmul(2.0, dadd(dadd(dmul(dmul(kap[0], kap[1]), m2[3]), dmul(dmul(kap[0], kap[2]), m2[4])),
+                                dmul(dmul(kap[1], kap[2]), m2[5]))));
+        const double m4 = dsub(dadd(dadd(dsub(E4, dmul(4.0, kE3)), dmul(dmul(2.0, kk), trm2)), dmul(4.0, km2k)),
+                               dmul(3.0, dmul(kk, kk)));
+        const double Cbar = dsub(ddiv(m4, dmul(10.0, dmul(Tg, Tg))), 0.5);
+        double Abar[6];
+        for (int i = 0; i < 6; ++i) Abar[i] = i < 3 ? dsub(ddiv(C[i], Tg), 1.0) : ddiv(C[i], Tg);
+        const double sq = dmul(Tg, __dsqrt_rn(Tg));
+        double Bbar[3];
+        for (int d = 0; d < 3; ++d) Bbar[d] = ddiv(dmul(0.5, m3[d]), sq);
+        const double c23 = 2.0 / 3.0;
+        double V[6];
+        for (int i = 0; i < 6; ++i) {
+          const double bb = dmul(Bbar[pd[i]], Bbar[pe[i]]);
+          V[i] = i < 3 ? dsub(dadd(1.0, Abar[i]), dmul(c23, bb)) : dsub(Abar[i], dmul(c23, bb));
+        }
+        bool realizable = false;
+        if (Cbar > 0.4) {
+          const double gam = ddiv(2.0, dmul(5.0, Cbar));
+          const double coef = ddiv(gam, dsub(1.0, gam));
+          double Vg[6];
+          for (int i = 0; i < 6; ++i) {
+            const double bb = dmul(Bbar[pd[i]], Bbar[pe[i]]);
+            Vg[i] = i < 3 ? dsub(dadd(1.0, Abar[i]), dmul(coef, bb)) : dsub(Abar[i], dmul(coef, bb));
+          }
+          realizable = psd3(Vg);
+        }
+        double up[6], dn[6];
+        for (int i = 0; i < 6; ++i) {
+          up[i] = i < 3 ? dsub(dadd(1.0, eta0), V[i]) : -V[i];
+          dn[i] = i < 3 ? dsub(V[i], dsub(1.0, eta0)) : V[i];
+        }
+        const bool near_euler = psd3(up) && psd3(dn);
+        mbits = (realizable ? 0 : 1) | (near_euler ? 0 : 2);
+        double ev[3];
+        eig3(V, ev);
+        // pack
+        for (int i = 0; i < 6; ++i) { o[5 + i] = Theta[i]; o[11 + i] = tau[i]; o[20 + i] = Abar[i]; o[30 + i] = V[i]; }
+        for (int d = 0; d < 3; ++d) { o[17 + d] = q[d]; o[26 + d] = Bbar[d]; o[36 + d] = ev[d]; }
+        o[29] = Cbar;
+        // Maxwellian parameters for pass 2
+        const double s = dmul(2.0 * 3.141592653589793, T);
+        const double CM = ddiv(rho, dmul(s, __dsqrt_rn(s)));
+        int eM;
+        frexp(CM, &eM);
+        const int P2 = kFixTop - (ef > eM ? ef : eM);
+        sh.bc[0] = CM;
+        sh.bc[1] = ddiv(1.0, dmul(2.0, T));
+        sh.bc[2] = h;
+        for (int d = 0; d < 3; ++d) sh.bc[3 + d] = u[d];
+        sh.ibc[0] = 1;
+        sh.ibc[1] = P2;
+      }
+    }
+    for (int i = 0; i < 40; ++i) out[i] = o[i];
+    sh.ibc[2] = mbits;
+  }
+  __syncthreads();
+  if (sh.ibc[0] == 0) {
+    if (tid == 0) *mask = uint8_t(sh.ibc[2]);
+    __syncthreads();
+    return;
+  }
+  // ---- pass 2: L1 distance to the Maxwellian (exact integer sum)
+  const double CM = sh.bc[0], inv2T = sh.bc[1], h = sh.bc[2];
+  const int P2 = sh.ibc[1];
+  if (tid < 3 * N) {
+    const int d = tid / N, j = tid % N;
+    const double x = dsub(dmul(h, double(j - half)), sh.bc[3 + d]);
+    sh.e[d][j] = own_exp(-dmul(dmul(x, x), inv2T));
+  }
+  __syncthreads();
+  if (tid < N) sh.E2[tid] = static_cast<unsigned long long>(__double2ll_rn(ldexp(sh.e[2][tid], kEBits)));
+  __syncthreads();
+  u128 l1acc = 0;
+  for (int row = tid; row < N * N; row += kMThreads) {
+    const int j0 = row / N, j1 = row % N;
+    const double A = dmul(dmul(CM, sh.e[0][j0]), sh.e[1][j1]);
+    const unsigned long long Af = static_cast<unsigned long long>(__double2ll_rn(ldexp(A, P2)));
+    const Tio* fr = f + size_t(row) * N;
+    for (int j2 = 0; j2 < N; ++j2) {
+      const long long F2 = fix_val(fr[j2], P2);
+      const unsigned long long E = sh.E2[j2];
+      unsigned long long lo = Af * E;
+      unsigned long long hi = __umul64hi(Af, E);
+      const unsigned long long add = 1ull << (kEBits - 1);
+      const unsigned long long lo2 = lo + add;
+      hi += (lo2 < lo) ? 1ull : 0ull;
+      const long long M = static_cast<long long>((hi << (64 - kEBits)) | (lo2 >> kEBits));
+      const long long dlt = F2 - M;
+      l1acc += static_cast<u128>(dlt < 0 ? -dlt : dlt);
+    }
+  }
+  i128 l1v[1] = {static_cast<i128>(l1acc)};
+  block_sum<1>(l1v, sh.red);
+  if (tid == 0) {
+    const double vol = dmul(dmul(h, h), h);
+    const double l1 = dmul(ldexp(i128_to_double(l1v[0]), -P2), vol);
+    out[39] = l1;
+    uint8_t mb = uint8_t(sh.ibc[2]);
+    if (l1 > delta0) mb |= 4;
+    *mask = mb;
+  }
+  __syncthreads();
+}
+
+template <typename Tio>
+__global__ void __launch_bounds__(kMThreads, 2) moments_kernel(const Tio* __restrict__ f, int N, double L,
+                                                            long long n_cells, double eta0, double delta0,
+                                                            coll_moments* mom, uint8_t* mask) {
+  __shared__ CellShared sh;
+  const size_t n3 = size_t(N) * N * N;
+  for (long long c = blockIdx.x; c < n_cells; c += gridDim.x)
+    moments_cell<Tio>(f + size_t(c) * n3, N, L, eta0, delta0, mom + c, mask + c, sh);
+}
+
+}  // namespace
+
+int launch_moments(const void* f, int io_f64, int N, double L, long long n_cells, double eta0, double delta0,
+                   coll_moments* mom, uint8_t* mask, void* stream) {
+  count_launches(1);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (io_f64)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, moments_kernel<double>, kMThreads, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, moments_kernel<float>, kMThreads, 0);
+  if (per < 1) per = 1;
+  long long grid = static_cast<long long>(sms) * per;
+  if (grid > n_cells) grid = n_cells;
+  if (io_f64)
+    moments_kernel<double><<<int(grid), kMThreads, 0, st>>>(static_cast<const double*>(f), N, L, n_cells, eta0,
+                                                            delta0, mom, mask);
+  else
+    moments_kernel<float><<<int(grid), kMThreads, 0, st>>>(static_cast<const float*>(f), N, L, n_cells, eta0,
+                                                           delta0, mom, mask);
+  return int(cudaGetLastError());
+}
+
+}  // namespace coll

@@ -1,0 +1,74 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol the
+headers declare, and its host-built multiplier tables match the oracle's."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2505_03360_gb300 import build as _build
+
+_build.build()
+from paper_2505_03360_gb300 import coll  # noqa: E402
+from oracle.kernel import Params, multipliers, nyquist_mask  # noqa: E402
+
+
+def test_library_exports_every_declared_symbol():
+    names = coll.header_functions()
+    assert "coll_eval_batch" in names and "moments_realizability" in names and len(names) >= 12
+    for n in names:
+        assert hasattr(coll._lib, n), n
+
+
+def test_status_strings():
+    for s in range(7):
+        assert coll.coll_status_string(s).startswith("COLL_")
+    assert "unknown" in coll.coll_status_string(99)
+
+
+def _compare_tables(N, L, lam, M, Mt, Mr, rule=0, S=0.0, tol=1e-13):
+    desc = coll.make_desc(N, L, S=S, lam=lam, M=M, Mtheta=Mt, Mr=Mr, sphere_rule=rule, prec="f64")
+    tab = coll.coll_plan_tables_host(desc)
+    p = Params(N=N, L=L, S=S, lam=lam, M=M, Mtheta=Mt, Mr=Mr, sphere_rule=rule)
+    m = multipliers(p)
+    H = N // 2
+    n3 = float(N) ** 3
+    assert tab.shape[0] == m.n_terms + 1
+    nyq = nyquist_mask(N)[:, :, :H]
+    for t in range(m.n_terms):
+        A = m.coef[t] * m.alpha[t][:, :, :H] / n3
+        B = m.alphap[t][:, :, :H] / n3
+        A[nyq] = 0
+        B[nyq] = 0
+        sig = np.abs(tab[t, ..., 1]).max() / np.abs(B).max()        # the balancing power of two
+        assert abs(math.log2(sig) - round(math.log2(sig))) < 1e-9
+        sa = np.abs(A).max()
+        sb = np.abs(B).max()
+        assert np.abs(tab[t, ..., 0] * sig - A).max() <= tol * sa, t
+        assert np.abs(tab[t, ..., 1] / sig - B).max() <= tol * sb, t
+        # balanced: the two factors have comparable size
+        assert 0.25 <= np.abs(tab[t, ..., 0]).max() / np.abs(tab[t, ..., 1]).max() <= 4.0
+    Lam = -m.lam_loss[:, :, :H] / n3
+    Lam[nyq] = 0
+    one = np.full((N, N, H), 1.0 / n3)
+    one[nyq] = 0
+    sig = np.abs(tab[-1, ..., 1]).max() / np.abs(one).max()
+    assert np.abs(tab[-1, ..., 0] * sig - Lam).max() <= tol * np.abs(Lam).max()
+    assert np.array_equal(tab[-1, ..., 1] / sig, one)
+
+
+def test_tables_hard_spheres_config2_shape():
+    _compare_tables(32, (3 + math.sqrt(2)) * 3, 1.0, 48, 4, 16)
+
+
+def test_tables_maxwell_config1_shape():
+    _compare_tables(16, (3 + math.sqrt(2)) * 3, 0.0, 32, 4, 8, S=6.0, tol=1e-12)
+
+
+def test_tables_paper_rule_and_N24():
+    _compare_tables(24, 8.0, 1.0, 32, 4, 8, rule=1, S=3.3)
+
+
+def test_tables_reject_bad_desc():
+    bad = coll.make_desc(16, 8.0, M=30, Mtheta=4)      # Mphi odd
+    with pytest.raises(coll.CollError):
+        coll.coll_plan_tables_host(bad)
