@@ -49,10 +49,17 @@ def fp64_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
     return sms * 4 * sm_mhz * 1e6 / 1e12
 
 
-def src_hash() -> str:
+KERNEL_SOURCES = {
+    "collision_f64_n32": ["collision_impl.cuh", "collision_layout.cuh", "fft.cuh", "twiddles.h", "coll_inst_d32.cu"],
+    "moments_f64": ["moments.cu"],
+}
+
+
+def src_hash(kernel_key: str) -> str:
+    """Hash of the sources a kernel is compiled from (a stale ncu traffic figure reads as null)."""
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2505_03360_gb300", "csrc", "*"))):
-        h.update(open(p, "rb").read())
+    for name in KERNEL_SOURCES[kernel_key]:
+        h.update(open(os.path.join(ROOT, "paper_2505_03360_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -127,7 +134,7 @@ def load_traffic(kernel_key: str):
     try:
         d = json.load(open(p))
         e = d.get(kernel_key)
-        if e and e.get("src_hash") == src_hash():
+        if e and e.get("src_hash") == src_hash(kernel_key):
             return e.get("dram_bytes_per_launch")
     except Exception:
         return None
@@ -185,7 +192,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     w = WORKLOAD
-    N, n = w["N"], w["cells"]
+    N, n = w["N"], args.cells
     f_host = synth.bimodal_batch(n, N, w["L"], seed=synth.BASE_SEED + 2 + 1000 * rank)
     f_pin = torch.from_numpy(f_host).pin_memory()
     f = f_pin.to(dev)
@@ -232,6 +239,12 @@ def run_ours(args, rank, world, local_rank):
         elapsed = float(t.item())
         dist.barrier()
 
+    if args.profile_only:
+        if rank == 0:
+            print(json.dumps({"profile_only": True, "cells": n, "ms_per_step": 1e3 * elapsed / args.steps,
+                              "collision_ms": coll_ms}), flush=True)
+        plan.close()
+        return
     # end to end through the C ABI from pinned host buffers: H2D f, evaluate, D2H Q + moments + mask
     Q_pin = torch.empty(Q.shape, dtype=Q.dtype).pin_memory()
     mom_pin = torch.empty(mom.shape, dtype=mom.dtype).pin_memory()
@@ -329,6 +342,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cells", type=int, default=WORKLOAD["cells"],
+                    help="cells per rank (default: the 4096-cell workload; smaller only for profiling)")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="time the main path only (no e2e, no FP32 variant): for short profiler captures")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -158,30 +158,34 @@ __device__ __forceinline__ bool psd3(const double* S) {
   return det >= 0.0;
 }
 
-// eigenvalues of a symmetric 3x3 matrix, ascending (trigonometric closed form)
+// eigenvalues of a symmetric 3x3 matrix, ascending: cyclic Jacobi rotations
+// (accurate to a few ulps of the matrix norm, also for clustered eigenvalues)
 __device__ void eig3(const double* S, double* ev) {
-  const double a = S[0], b = S[1], c = S[2], d = S[3], e = S[4], f = S[5];
-  const double p1 = d * d + e * e + f * f;
-  const double q = (a + b + c) / 3.0;
-  if (p1 == 0.0) {
-    double x = a, y = b, z = c, t;
-    if (x > y) { t = x; x = y; y = t; }
-    if (y > z) { t = y; y = z; z = t; }
-    if (x > y) { t = x; x = y; y = t; }
-    ev[0] = x; ev[1] = y; ev[2] = z;
-    return;
+  double a[3][3] = {{S[0], S[3], S[4]}, {S[3], S[1], S[5]}, {S[4], S[5], S[2]}};
+  for (int sweep = 0; sweep < 16; ++sweep) {
+    const double off = fabs(a[0][1]) + fabs(a[0][2]) + fabs(a[1][2]);
+    if (off == 0.0) break;
+    for (int pq = 0; pq < 3; ++pq) {
+      const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+      const double apq = a[p][q];
+      if (apq == 0.0) continue;
+      const double theta = (a[q][q] - a[p][p]) / (2.0 * apq);
+      const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+      const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+      a[p][p] -= t * apq;
+      a[q][q] += t * apq;
+      a[p][q] = a[q][p] = 0.0;
+      const int r = 3 - p - q;
+      const double arp = a[r][p], arq = a[r][q];
+      a[r][p] = a[p][r] = c * arp - s * arq;
+      a[r][q] = a[q][r] = s * arp + c * arq;
+    }
   }
-  const double p2 = (a - q) * (a - q) + (b - q) * (b - q) + (c - q) * (c - q) + 2.0 * p1;
-  const double p = sqrt(p2 / 6.0);
-  const double B0 = (a - q) / p, B1 = (b - q) / p, B2 = (c - q) / p, B3 = d / p, B4 = e / p, B5 = f / p;
-  const double detB = B0 * (B1 * B2 - B5 * B5) - B3 * (B3 * B2 - B5 * B4) + B4 * (B3 * B5 - B1 * B4);
-  double r = detB / 2.0;
-  r = r < -1.0 ? -1.0 : (r > 1.0 ? 1.0 : r);
-  const double phi = acos(r) / 3.0;
-  const double e1 = q + 2.0 * p * cos(phi);
-  const double e3 = q + 2.0 * p * cos(phi + 2.0943951023931954923);
-  const double e2 = 3.0 * q - e1 - e3;
-  ev[0] = e3; ev[1] = e2; ev[2] = e1;
+  double x = a[0][0], y = a[1][1], z = a[2][2], tt;
+  if (x > y) { tt = x; x = y; y = tt; }
+  if (y > z) { tt = y; y = z; z = tt; }
+  if (x > y) { tt = x; x = y; y = tt; }
+  ev[0] = x; ev[1] = y; ev[2] = z;
 }
 
 __device__ __forceinline__ i128 warp_sum(i128 v) {
