@@ -137,6 +137,30 @@ coll_status coll_eval_batch(coll_plan plan, const void* f, void* Q, int64_t n_ce
                             void* ws, size_t ws_bytes, coll_stream stream);
 
 /*
+ * coll_eval_batch_static -- coll_eval_batch without a caller-provided
+ * workspace, for callers that cannot allocate device memory: code that runs
+ * while a CUDA graph is being captured (cudaMalloc is not allowed there),
+ * hosts whose own allocator must own every device allocation and cannot hand
+ * out a raw scratch block, or latency-critical loops that must never risk an
+ * allocation.  The paper has no counterpart; this is a library convenience.
+ *
+ * The kernel's scratch is a fixed 32 MiB device array inside libcoll.so (every
+ * GPU that loads the library keeps it until the process exits).  Its device
+ * address is looked up on the first call on each device, with that device
+ * current; make that first call before any stream capture.  The call
+ * allocates and frees nothing.  If one CTA's scratch for this plan exceeds
+ * 32 MiB it returns COLL_ENOMEM; otherwise the grid is capped so that the
+ * scratch fits, so it may run fewer CTAs (and be slower) than
+ * coll_eval_batch.  All calls share the array: the kernel clears what it
+ * accumulates before using it, but calls whose launches overlap on the GPU
+ * (different streams or host threads) race on the array and must be
+ * serialised by the caller.  Arguments, errors and results are otherwise
+ * those of coll_eval_batch.
+ */
+coll_status coll_eval_batch_static(coll_plan plan, const void* f, void* Q, int64_t n_cells,
+                                   coll_stream stream);
+
+/*
  * Ragged batch: n_groups groups, each with its own plan (different N and/or
  * precision), its own f and Q arrays and cells_per_group[g] cells, evaluated
  * in ONE persistent launch that schedules the largest cells first.  All plans

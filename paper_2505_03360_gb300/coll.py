@@ -56,6 +56,7 @@ def _load():
         "coll_plan_terms": (I32, [P, ctypes.POINTER(I32)]),
         "coll_workspace_size": (I32, [P, I64, ctypes.POINTER(SZ)]),
         "coll_eval_batch": (I32, [P, P, P, I64, P, SZ, P]),
+        "coll_eval_batch_static": (I32, [P, P, P, I64, P]),
         "coll_ragged_workspace_size": (I32, [ctypes.POINTER(coll_cell_group), ctypes.POINTER(I64), I32,
                                              ctypes.POINTER(SZ)]),
         "coll_eval_ragged": (I32, [ctypes.POINTER(coll_cell_group), ctypes.POINTER(I64), I32, P, SZ, P]),
@@ -146,6 +147,14 @@ def coll_eval_batch(plan: int, f, Q, n_cells: int, ws, ws_bytes: int = None, str
                               _stream_ptr(stream))
     if check:
         _check(st, "coll_eval_batch")
+    return st
+
+
+def coll_eval_batch_static(plan: int, f, Q, n_cells: int, stream=None, check=True) -> int:
+    """coll_eval_batch with the library's fixed device scratch (no allocation)."""
+    st = _lib.coll_eval_batch_static(ctypes.c_void_p(plan), _ptr(f), _ptr(Q), int(n_cells), _stream_ptr(stream))
+    if check:
+        _check(st, "coll_eval_batch_static")
     return st
 
 
