@@ -19,9 +19,9 @@ HEADER = os.path.join(os.path.dirname(PKG), "include", "coll.h")
 HEADERS = [HEADER, os.path.join(os.path.dirname(PKG), "include", "coll_debug.h")]
 
 COLL_OK, COLL_EINVAL, COLL_EUNSUPPORTED, COLL_ENOMEM, COLL_ECUDA, COLL_ETIMEOUT, COLL_ENONFINITE = range(7)
-COLL_F64, COLL_F32, COLL_MIXED_F16X2, COLL_MIXED_BF16X3 = range(4)
-PREC = {"f64": COLL_F64, "f32": COLL_F32, "mixed": COLL_MIXED_F16X2, "mixed_f16x2": COLL_MIXED_F16X2,
-        "mixed_bf16x3": COLL_MIXED_BF16X3}
+COLL_F64, COLL_F32, COLL_MIXED_F16X2, COLL_MIXED_BF16X3, COLL_F32X2 = range(5)
+PREC = {"f64": COLL_F64, "f32": COLL_F32, "mixed_f16x2": COLL_MIXED_F16X2,
+        "mixed_bf16x3": COLL_MIXED_BF16X3, "f32x2": COLL_F32X2}
 
 
 class CollError(RuntimeError):
@@ -114,7 +114,7 @@ def make_desc(N, L, S=0.0, lam=1.0, b0=-1.0, M=48, Mtheta=4, Mr=16, sphere_rule=
               io_dtype=None) -> coll_plan_desc:
     p = PREC[prec] if isinstance(prec, str) else int(prec)
     if io_dtype is None:
-        io_dtype = 0 if p == COLL_F64 else 1
+        io_dtype = 0 if p in (COLL_F64, COLL_F32X2) else 1
     return coll_plan_desc(int(N), float(L), float(S), float(lam), float(b0), int(M), int(Mtheta), int(Mr),
                           int(sphere_rule), int(dealias), p, int(io_dtype))
 

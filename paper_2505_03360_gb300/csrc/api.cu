@@ -21,8 +21,8 @@ using namespace coll;
 
 namespace {
 
-bool valid_N(int N, bool f64) {
-  if (f64) return N == 16 || N == 24 || N == 32;
+bool valid_N(int N, int ctype) {
+  if (ctype != kCF32) return N == 16 || N == 24 || N == 32;
   return N == 16 || N == 24 || N == 32 || N == 48 || N == 64;
 }
 
@@ -61,12 +61,13 @@ coll_status coll_plan_create(const coll_plan_desc* desc, coll_plan* out) {
       d.Mtheta <= 0 || d.Mr <= 0 || d.Mr > 256 || (d.io_dtype != 0 && d.io_dtype != 1) ||
       (d.sphere_rule != 0 && d.sphere_rule != 1) || (d.dealias != 0 && d.dealias != 1))
     return COLL_EINVAL;
-  if (d.prec != COLL_F64 && d.prec != COLL_F32 && d.prec != COLL_MIXED_F16X2 && d.prec != COLL_MIXED_BF16X3)
+  if (d.prec != COLL_F64 && d.prec != COLL_F32 && d.prec != COLL_MIXED_F16X2 && d.prec != COLL_MIXED_BF16X3 &&
+      d.prec != COLL_F32X2)
     return COLL_EINVAL;
   if (d.dealias) return COLL_EUNSUPPORTED;
   if (d.prec == COLL_MIXED_F16X2 || d.prec == COLL_MIXED_BF16X3) return COLL_EUNSUPPORTED;
-  const bool f64 = d.prec == COLL_F64;
-  if (!valid_N(d.N, f64)) return COLL_EUNSUPPORTED;
+  const int ctype = d.prec == COLL_F64 ? kCF64 : (d.prec == COLL_F32 ? kCF32 : kCDF);
+  if (!valid_N(d.N, ctype)) return COLL_EUNSUPPORTED;
 
   HostTables ht;
   coll_status st = build_tables(d, &ht);
@@ -75,28 +76,37 @@ coll_status coll_plan_create(const coll_plan_desc* desc, coll_plan* out) {
   coll_plan_s* p = new (std::nothrow) coll_plan_s();
   if (!p) return COLL_ENOMEM;
   p->d = d;
-  p->f64 = f64;
+  p->ctype = ctype;
   p->io_f64 = d.io_dtype == 0;
   p->n_terms = ht.n_terms;
   if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return COLL_ECUDA; }
   cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
-  if (!layout_info(d.N, f64, &p->lay)) { delete p; return COLL_EUNSUPPORTED; }
+  if (!layout_info(d.N, ctype, &p->lay)) { delete p; return COLL_EUNSUPPORTED; }
   int per = 0;
-  if (collision_max_ctas_per_sm(d.N, f64, p->io_f64, &per) != 0 || per < 1) {
+  if (collision_max_ctas_per_sm(d.N, ctype, p->io_f64, &per) != 0 || per < 1) {
     delete p;
     return COLL_ECUDA;
   }
   p->ctas_per_sm = per;
 
   const size_t n = ht.tab.size();
-  p->tab_bytes = n * (f64 ? sizeof(double) : sizeof(float));
+  p->tab_bytes = n * (ctype == kCF32 ? sizeof(float) : sizeof(double));
   if (cudaMalloc(&p->tab_dev, p->tab_bytes) != cudaSuccess) { delete p; return COLL_ENOMEM; }
   cudaError_t e;
-  if (f64) {
+  if (ctype == kCF64) {
     e = cudaMemcpy(p->tab_dev, ht.tab.data(), p->tab_bytes, cudaMemcpyHostToDevice);
-  } else {
+  } else if (ctype == kCF32) {
     std::vector<float> tf(n);
     for (size_t i = 0; i < n; ++i) tf[i] = float(ht.tab[i]);
+    e = cudaMemcpy(p->tab_dev, tf.data(), p->tab_bytes, cudaMemcpyHostToDevice);
+  } else {
+    // float pairs: head = nearest float, tail = nearest float to the remainder
+    std::vector<float> tf(2 * n);
+    for (size_t i = 0; i < n; ++i) {
+      const float h = float(ht.tab[i]);
+      tf[2 * i] = h;
+      tf[2 * i + 1] = float(ht.tab[i] - double(h));
+    }
     e = cudaMemcpy(p->tab_dev, tf.data(), p->tab_bytes, cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->status_dev), sizeof(int));
@@ -167,7 +177,7 @@ coll_status coll_eval_batch(coll_plan p, const void* f, void* Q, int64_t n_cells
   a.ws = ws;
   a.ws_per_cta = p->lay.ws_bytes_per_cta();
   a.status = p->status_dev;
-  const int e = launch_collision(p->d.N, p->f64, p->io_f64, a, grid, stream);
+  const int e = launch_collision(p->d.N, p->ctype, p->io_f64, a, grid, stream);
   return e == 0 ? COLL_OK : COLL_ECUDA;
 }
 

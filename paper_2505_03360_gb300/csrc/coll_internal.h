@@ -38,8 +38,11 @@ struct LayoutInfo {
   }
 };
 
-// Returns false if (N, is_f64) has no kernel instantiation.
-bool layout_info(int N, bool is_f64, LayoutInfo* out);
+// compute types of the collision kernel
+enum CType : int { kCF64 = 0, kCF32 = 1, kCDF = 2 };
+
+// Returns false if (N, ctype) has no kernel instantiation.
+bool layout_info(int N, int ctype, LayoutInfo* out);
 
 struct CollArgs {
   const void* f;
@@ -56,8 +59,8 @@ struct CollArgs {
 enum : int { kStatusNonFinite = 1, kStatusTimeout = 2 };
 
 // Launchers (collision.cu); return cudaError_t as int.
-int launch_collision(int N, bool f64, bool io_f64, const CollArgs& a, int grid, void* stream);
-int collision_max_ctas_per_sm(int N, bool f64, bool io_f64, int* ctas);
+int launch_collision(int N, int ctype, bool io_f64, const CollArgs& a, int grid, void* stream);
+int collision_max_ctas_per_sm(int N, int ctype, bool io_f64, int* ctas);
 
 // Ragged launch: one persistent kernel over mixed N (collision.cu).
 struct RaggedItem {            // one group of cells with the same plan
@@ -95,7 +98,7 @@ struct coll_plan_s {
   coll_plan_desc d;
   int device;
   int n_terms;
-  bool f64;          // compute precision FP64
+  int ctype;         // compute type of the transforms (coll::CType)
   bool io_f64;       // f / Q element type
   void* tab_dev;     // device tables in the compute type
   size_t tab_bytes;

@@ -26,8 +26,16 @@ template <int N, typename T> LayoutInfo make_info() {
   return i;
 }
 
-bool layout_info(int N, bool f64, LayoutInfo* out) {
-  if (f64) {
+bool layout_info(int N, int ctype, LayoutInfo* out) {
+  if (ctype == kCDF) {
+    switch (N) {
+      case 16: *out = make_info<16, df>(); return true;
+      case 24: *out = make_info<24, df>(); return true;
+      case 32: *out = make_info<32, df>(); return true;
+      default: return false;
+    }
+  }
+  if (ctype == kCF64) {
     switch (N) {
       case 16: *out = make_info<16, double>(); return true;
       case 24: *out = make_info<24, double>(); return true;
@@ -46,7 +54,21 @@ bool layout_info(int N, bool f64, LayoutInfo* out) {
 }
 
 #define COLL_DISPATCH(FN, ...)                                                              \
-  if (f64) {                                                                                \
+  if (ctype == kCDF) {                                                                      \
+    if (io_f64) {                                                                           \
+      switch (N) {                                                                          \
+        case 16: return FN<16, df, double>(__VA_ARGS__);                                    \
+        case 24: return FN<24, df, double>(__VA_ARGS__);                                    \
+        case 32: return FN<32, df, double>(__VA_ARGS__);                                    \
+      }                                                                                     \
+    } else {                                                                                \
+      switch (N) {                                                                          \
+        case 16: return FN<16, df, float>(__VA_ARGS__);                                     \
+        case 24: return FN<24, df, float>(__VA_ARGS__);                                     \
+        case 32: return FN<32, df, float>(__VA_ARGS__);                                     \
+      }                                                                                     \
+    }                                                                                       \
+  } else if (ctype == kCF64) {                                                              \
     if (io_f64) {                                                                           \
       switch (N) {                                                                          \
         case 16: return FN<16, double, double>(__VA_ARGS__);                                \
@@ -81,13 +103,13 @@ bool layout_info(int N, bool f64, LayoutInfo* out) {
   }                                                                                         \
   return int(cudaErrorInvalidValue);
 
-int launch_collision(int N, bool f64, bool io_f64, const CollArgs& a, int grid, void* stream) {
+int launch_collision(int N, int ctype, bool io_f64, const CollArgs& a, int grid, void* stream) {
   count_launches(1);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   COLL_DISPATCH(launch_one, a, grid, st)
 }
 
-int collision_max_ctas_per_sm(int N, bool f64, bool io_f64, int* ctas) {
+int collision_max_ctas_per_sm(int N, int ctype, bool io_f64, int* ctas) {
   COLL_DISPATCH(occupancy_one, ctas)
 }
 

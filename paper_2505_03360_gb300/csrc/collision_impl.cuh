@@ -15,13 +15,17 @@
 //   F1  rows along axis 2: two real rows packed per complex FFT, split into
 //       their half spectra                                   -> Fh
 //   F2  axis 1, F3 axis 0 (complex, in place on Fh)
-//   per term t, per v0-slab s:
+//   per v0-slab s (planes v0 = s mod S0), per term t:
 //   P1  axis 0 inverse for every (k1, k2) pencil of the full spectrum, built on
 //       the fly from Fh (Hermitian partner for k2 > N/2) times (A + iB); only
-//       the outputs v0 = s mod S0 are formed (decimation in frequency)  -> W
+//       the outputs of slab s are formed (decimation in frequency)   -> W
 //   P2  axis 1 inverse on the slab (in place)
-//   P3  axis 2 inverse per (v0, v1) row; G += Re * Im; the loss term writes
-//       Q = G + Re * Im and clears G for the next cell
+//   P3  axis 2 inverse per (v0, v1) row; G_s += Re * Im; the loss term
+//       writes Q = G_s + Re * Im for the slab's planes
+// Slabs outermost keep only one slab of the gain accumulator live, so it
+// stays in shared memory.  F1, F2, F3, P2 and P3 share one FFT body (a
+// non-inlined pass function; forward transforms by conjugation) to keep the
+// instruction footprint small.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -32,6 +36,147 @@
 namespace coll {
 
 template <typename Tio, typename T> __device__ __forceinline__ T ld_io(const Tio* p) { return T(*p); }
+template <> __device__ __forceinline__ df ld_io<double, df>(const double* p) { return df_from_double(*p); }
+template <> __device__ __forceinline__ df ld_io<float, df>(const float* p) { return df_from_float(*p); }
+template <typename Tio, typename T> __device__ __forceinline__ Tio to_io(T v) { return Tio(v); }
+template <> __device__ __forceinline__ double to_io<double, df>(df v) { return df_to_double(v); }
+template <> __device__ __forceinline__ float to_io<float, df>(df v) { return __fadd_rn(v.h, v.l); }
+__device__ __forceinline__ bool finite_v(double x) { return ::isfinite(x); }
+__device__ __forceinline__ bool finite_v(float x) { return ::isfinite(x); }
+__device__ __forceinline__ bool finite_v(df x) { return isfinite(x); }
+
+enum PassMode : int { kPassF1 = 0, kPassFwd = 1, kPassInv = 2, kPassP3 = 3 };
+
+// One pass of length-N register FFTs over a set of pencils.  Pencil pid maps to
+// (a, b) = (pid / inner, pid % inner) and starts at base + a*s_outer + b*s_inner;
+// its elements are s_elem apart.  Modes:
+//   kPassF1   two real rows of f packed into one complex FFT, split into the
+//             two half spectra (rows 2 pid, 2 pid + 1 of Fh = base)
+//   kPassFwd  forward transform in place (as conj(IFFT(conj x)))
+//   kPassInv  inverse transform in place; pencils with b == skip_b are zero
+//   kPassP3   inverse transform of W rows, then G += Re*Im (or, on the last
+//             term, Q = G + Re*Im for the planes v0 = s + S0 m)
+// Returns true if a non-finite output was written.
+template <int N, typename T, typename Tio>
+__device__ __noinline__ bool run_pass(int mode, typename C2<T>::type* base, int count, int inner, int s_outer,
+                                      int s_inner, int s_elem, int skip_b, const Tio* __restrict__ f, Tio* Q,
+                                      T* G, int s, int S0, int fh_row, bool last) {
+  using V2 = typename C2<T>::type;
+  constexpr int H = N / 2;
+  bool bad = false;
+  for (int pid = threadIdx.x; pid < count; pid += kThreads) {
+    const int a = pid / inner, b = pid % inner;
+    if (mode == kPassInv && b == skip_b) continue;
+    T xr[N], xi[N];
+    V2* p = base + size_t(a) * s_outer + size_t(b) * s_inner;
+    if (mode == kPassF1) {
+      const Tio* r0 = f + size_t(2 * pid) * N;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        xr[j] = ld_io<Tio, T>(r0 + j);
+        xi[j] = -ld_io<Tio, T>(r0 + N + j);     // conj for the forward transform
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const V2 v = p[size_t(j) * s_elem];
+        xr[j] = v.x;
+        xi[j] = (mode == kPassFwd) ? -v.y : v.y;
+      }
+    }
+    fft<N, +1, T>(xr, xi);
+    if (mode == kPassF1) {
+      // Z = conj(xi) is the forward transform of row0 + i row1; split
+      V2* o0 = base + size_t(2 * pid) * fh_row;
+      V2* o1 = o0 + fh_row;
+#pragma unroll
+      for (int k = 0; k < H; ++k) {
+        const int kn = (N - k) % N;
+        const T zrk = xr[k], zik = -xi[k], zrn = xr[kn], zin = -xi[kn];
+        o0[k] = V2{half(zrk + zrn), half(zik - zin)};
+        o1[k] = V2{half(zik + zin), half(zrn - zrk)};
+      }
+    } else if (mode == kPassFwd || mode == kPassInv) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) p[size_t(j) * s_elem] = V2{xr[j], (mode == kPassFwd) ? -xi[j] : xi[j]};
+    } else {
+      T* g = G + (size_t(a) * N + b) * N;
+      if (!last) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) g[j] += xr[j] * xi[j];
+      } else {
+        const int v0 = s + S0 * a;
+        Tio* q = Q + (size_t(v0) * N + b) * N;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const T val = g[j] + xr[j] * xi[j];
+          bad |= !finite_v(val);
+          q[j] = to_io<Tio, T>(val);
+        }
+      }
+    }
+  }
+  return bad;
+}
+
+// P1: axis-0 inverse of (A + iB) F for every full-spectrum pencil (k1, k2),
+// forming only the outputs v0 = s + S0 m (decimation in frequency):
+//   y[k'] = w_N^{s k'} sum_q x[k' + q NS] e^{2 pi i s q / S0},  then an NS-point IFFT.
+template <int N, typename T>
+__device__ __noinline__ void run_p1(const typename C2<T>::type* __restrict__ tb, const typename C2<T>::type* Fh,
+                                    typename C2<T>::type* W, int s) {
+  using Ly = Lay<N, T>;
+  using V2 = typename C2<T>::type;
+  constexpr int H = Ly::H, FR = Ly::FH_ROW, WR = Ly::W_ROW, S0 = Ly::S0, NS = Ly::NS;
+  for (int pid = threadIdx.x; pid < N * N; pid += kThreads) {
+    const int k1 = pid / N, k2 = pid % N;
+    T yr[NS], yi[NS];
+    if (k2 == H || k1 == H) {
+#pragma unroll
+      for (int m = 0; m < NS; ++m) { yr[m] = T{}; yi[m] = T{}; }
+    } else {
+      const bool up = k2 > H;
+      const int k2s = up ? N - k2 : k2;
+      const int k1s = up ? (N - k1) % N : k1;
+#pragma unroll
+      for (int kp = 0; kp < NS; ++kp) {
+        T ar = T{}, ai = T{};
+#pragma unroll
+        for (int q = 0; q < S0; ++q) {
+          const int k0 = kp + q * NS;
+          const int k0s = up ? (N - k0) % N : k0;
+          const size_t idx = (size_t(k0s) * N + k1s);
+          const V2 F = Fh[idx * FR + k2s];
+          const V2 AB = tb[idx * H + k2s];
+          const T fr = F.x, fi = up ? -F.y : F.y;   // conj for the Hermitian partner
+          T xr = AB.x * fr - AB.y * fi;
+          T xi = AB.x * fi + AB.y * fr;
+          if (S0 > 1 && q > 0) {
+            const int n = (s * q * (192 / S0)) % 192;
+            const T c = Tw<T>::c(n), sn = Tw<T>::s(n);
+            const T rr = xr * c - xi * sn;
+            xi = xr * sn + xi * c;
+            xr = rr;
+          }
+          ar = ar + xr;
+          ai = ai + xi;
+        }
+        if (S0 > 1) {
+          const int n = (s * kp * (192 / N)) % 192;
+          const T c = Tw<T>::c(n), sn = Tw<T>::s(n);
+          const T rr = ar * c - ai * sn;
+          ai = ar * sn + ai * c;
+          ar = rr;
+        }
+        yr[kp] = ar;
+        yi[kp] = ai;
+      }
+      fft<NS, +1, T>(yr, yi);
+    }
+#pragma unroll
+    for (int m = 0; m < NS; ++m) W[(size_t(m) * N + k1) * WR + k2] = V2{yr[m], yi[m]};
+  }
+}
 
 // ------------------------------------------------------------ per-cell body
 // smem: dynamic shared memory base; wsc: this CTA's workspace slice.
@@ -43,7 +188,6 @@ __device__ __forceinline__ void process_cell(const Tio* __restrict__ f, Tio* __r
   using Cf = Cfg<N, T>;
   using V2 = typename C2<T>::type;
   constexpr int H = Ly::H, FR = Ly::FH_ROW, WR = Ly::W_ROW, S0 = Ly::S0, NS = Ly::NS;
-  const int tid = threadIdx.x;
 
   unsigned char* sp = smem;
   unsigned char* gp = wsc;
@@ -53,168 +197,33 @@ __device__ __forceinline__ void process_cell(const Tio* __restrict__ f, Tio* __r
   if (Cf::FH) sp += Ly::round16(Ly::FH_BYTES); else gp += Ly::round16(Ly::FH_BYTES);
   T* G = reinterpret_cast<T*>(Cf::G ? sp : gp);
 
-  // ---- F1: real rows along axis 2, two per complex FFT -> half spectra
-  for (int pid = tid; pid < N * N / 2; pid += kThreads) {
-    const int r0 = 2 * pid, r1 = 2 * pid + 1;
-    T zr[N], zi[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      zr[j] = ld_io<Tio, T>(f + size_t(r0) * N + j);
-      zi[j] = ld_io<Tio, T>(f + size_t(r1) * N + j);
-    }
-    fft<N, -1, T>(zr, zi);
-    V2* o0 = Fh + size_t(r0) * FR;
-    V2* o1 = Fh + size_t(r1) * FR;
-#pragma unroll
-    for (int k = 0; k < H; ++k) {
-      const int kn = (N - k) % N;
-      const T hr = T(0.5) * (zr[k] + zr[kn]), hi = T(0.5) * (zi[k] - zi[kn]);
-      const T gr = T(0.5) * (zi[k] + zi[kn]), gi = T(0.5) * (zr[kn] - zr[k]);
-      o0[k] = V2{hr, hi};
-      o1[k] = V2{gr, gi};
-    }
-  }
+  // forward half spectrum: rows (F1), axis 1 (F2), axis 0 (F3)
+  run_pass<N, T, Tio>(kPassF1, Fh, N * N / 2, 1, 0, 0, 1, -1, f, Q, G, 0, S0, FR, false);
   __syncthreads();
-  // ---- F2: axis 1 (stride FR), pencils (j0, k2)
-  for (int pid = tid; pid < N * H; pid += kThreads) {
-    const int j0 = pid / H, k2 = pid % H;
-    V2* p = Fh + size_t(j0) * N * FR + k2;
-    T xr[N], xi[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) { V2 v = p[size_t(j) * FR]; xr[j] = v.x; xi[j] = v.y; }
-    fft<N, -1, T>(xr, xi);
-#pragma unroll
-    for (int j = 0; j < N; ++j) p[size_t(j) * FR] = V2{xr[j], xi[j]};
-  }
+  run_pass<N, T, Tio>(kPassFwd, Fh, N * H, H, N * FR, 1, FR, -1, f, Q, G, 0, S0, FR, false);
   __syncthreads();
-  // ---- F3: axis 0 (stride N*FR), pencils (k1, k2)
-  for (int pid = tid; pid < N * H; pid += kThreads) {
-    const int k1 = pid / H, k2 = pid % H;
-    V2* p = Fh + size_t(k1) * FR + k2;
-    T xr[N], xi[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) { V2 v = p[size_t(j) * N * FR]; xr[j] = v.x; xi[j] = v.y; }
-    fft<N, -1, T>(xr, xi);
-#pragma unroll
-    for (int j = 0; j < N; ++j) p[size_t(j) * N * FR] = V2{xr[j], xi[j]};
-  }
+  run_pass<N, T, Tio>(kPassFwd, Fh, N * H, H, FR, 1, N * FR, -1, f, Q, G, 0, S0, FR, false);
   __syncthreads();
 
-  for (int t = 0; t < n_terms; ++t) {
-    const V2* __restrict__ tb = tab + size_t(t) * N * N * H;
-    const bool last = (t == n_terms - 1);
-    for (int s = 0; s < S0; ++s) {
-      // ---- P1: axis-0 inverse of (A + iB) F for every full-spectrum pencil
-      for (int pid = tid; pid < N * N; pid += kThreads) {
-        const int k1 = pid / N, k2 = pid % N;
-        T yr[NS], yi[NS];
-        if (k2 == H || k1 == H) {
-#pragma unroll
-          for (int m = 0; m < NS; ++m) { yr[m] = T(0); yi[m] = T(0); }
-        } else {
-          const bool up = k2 > H;
-          const int k2s = up ? N - k2 : k2;
-          const int k1s = up ? (N - k1) % N : k1;
-          const T cs = up ? T(-1) : T(1);          // conj for the Hermitian partner
-#pragma unroll
-          for (int kp = 0; kp < NS; ++kp) {
-            T ar = T(0), ai = T(0);
-#pragma unroll
-            for (int q = 0; q < S0; ++q) {
-              const int k0 = kp + q * NS;
-              const int k0s = up ? (N - k0) % N : k0;
-              const size_t idx = (size_t(k0s) * N + k1s);
-              const V2 F = Fh[idx * FR + k2s];
-              const V2 AB = tb[idx * H + k2s];
-              const T fr = F.x, fi = cs * F.y;
-              T xr = AB.x * fr - AB.y * fi;
-              T xi = AB.x * fi + AB.y * fr;
-              if (S0 > 1 && q > 0) {
-                const int n = (s * q * (192 / S0)) % 192;
-                const T c = Tw<T>::c(n), sn = Tw<T>::s(n);
-                const T rr = xr * c - xi * sn;
-                xi = xr * sn + xi * c;
-                xr = rr;
-              }
-              ar += xr;
-              ai += xi;
-            }
-            if (S0 > 1) {
-              const int n = (s * kp * (192 / N)) % 192;
-              const T c = Tw<T>::c(n), sn = Tw<T>::s(n);
-              const T rr = ar * c - ai * sn;
-              ai = ar * sn + ai * c;
-              ar = rr;
-            }
-            yr[kp] = ar;
-            yi[kp] = ai;
-          }
-          fft<NS, +1, T>(yr, yi);
-        }
-#pragma unroll
-        for (int m = 0; m < NS; ++m) W[(size_t(m) * N + k1) * WR + k2] = V2{yr[m], yi[m]};
-      }
+  for (int s = 0; s < S0; ++s) {
+    for (int i = threadIdx.x; i < NS * N * N; i += kThreads) G[i] = T{};
+    __syncthreads();
+    for (int t = 0; t < n_terms; ++t) {
+      run_p1<N, T>(tab + size_t(t) * N * N * H, Fh, W, s);
       __syncthreads();
-      // ---- P2: axis-1 inverse within the slab, pencils (m, k2)
-      for (int pid = tid; pid < NS * N; pid += kThreads) {
-        const int m = pid / N, k2 = pid % N;
-        if (k2 == H) continue;                      // Nyquist plane stays zero
-        V2* p = W + size_t(m) * N * WR + k2;
-        T xr[N], xi[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) { V2 v = p[size_t(j) * WR]; xr[j] = v.x; xi[j] = v.y; }
-        fft<N, +1, T>(xr, xi);
-#pragma unroll
-        for (int j = 0; j < N; ++j) p[size_t(j) * WR] = V2{xr[j], xi[j]};
-      }
+      run_pass<N, T, Tio>(kPassInv, W, NS * N, N, N * WR, 1, WR, H, f, Q, G, s, S0, FR, false);
       __syncthreads();
-      // ---- P3: axis-2 inverse per row; accumulate Re * Im
-      for (int pid = tid; pid < NS * N; pid += kThreads) {
-        const int m = pid / N, v1 = pid % N;
-        const V2* p = W + (size_t(m) * N + v1) * WR;
-        T xr[N], xi[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) { V2 v = p[j]; xr[j] = v.x; xi[j] = v.y; }
-        fft<N, +1, T>(xr, xi);
-        const int v0 = s + S0 * m;
-        T* g = G + (size_t(v0) * N + v1) * N;
-        if (!last) {
-#pragma unroll
-          for (int j = 0; j < N; ++j) g[j] += xr[j] * xi[j];
-        } else {
-          Tio* q = Q + (size_t(v0) * N + v1) * N;
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            const T val = g[j] + xr[j] * xi[j];
-            bad |= !isfinite(val);
-            q[j] = Tio(val);
-            g[j] = T(0);
-          }
-        }
-      }
+      bad |= run_pass<N, T, Tio>(kPassP3, W, NS * N, N, N * WR, WR, 1, -1, f, Q, G, s, S0, FR,
+                                 t == n_terms - 1);
       __syncthreads();
     }
   }
-}
-
-template <int N, typename T>
-__device__ __forceinline__ void zero_gain(unsigned char* smem, unsigned char* wsc) {
-  using Ly = Lay<N, T>;
-  using Cf = Cfg<N, T>;
-  unsigned char* sp = smem;
-  unsigned char* gp = wsc;
-  if (Cf::W) sp += Ly::round16(Ly::W_BYTES); else gp += Ly::round16(Ly::W_BYTES);
-  if (Cf::FH) sp += Ly::round16(Ly::FH_BYTES); else gp += Ly::round16(Ly::FH_BYTES);
-  T* G = reinterpret_cast<T*>(Cf::G ? sp : gp);
-  for (int i = threadIdx.x; i < N * N * N; i += kThreads) G[i] = T(0);
 }
 
 template <int N, typename T, typename Tio>
 __global__ void __launch_bounds__(kThreads, 1) collision_kernel(CollArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* wsc = static_cast<unsigned char*>(a.ws) + size_t(blockIdx.x) * a.ws_per_cta;
-  zero_gain<N, T>(smem, wsc);
-  __syncthreads();
   bool bad = false;
   const auto* tab = static_cast<const typename C2<T>::type*>(a.tab);
   for (long long c = blockIdx.x; c < a.n_cells; c += gridDim.x) {

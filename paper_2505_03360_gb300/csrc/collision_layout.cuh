@@ -3,41 +3,58 @@
 
 #include <cstddef>
 
+#include "dfloat.cuh"
+
 namespace coll {
 
 template <typename T> struct C2;
 template <> struct C2<double> { using type = double2; };
 template <> struct C2<float> { using type = float2; };
+template <> struct C2<df> { using type = cdf; };
 
 // ----------------------------------------------------------------- layouts
+// Per (N, compute type): S0 v0-slabs; which arrays live in shared memory
+// (W = one slab of the per-term spectrum, Fh = forward half spectrum,
+// G = one slab of the gain accumulator); whether Fh rows are padded.
 template <int N, typename T> struct Cfg;
-//                 S0  W_smem Fh_smem G_smem
-template <> struct Cfg<16, double> { static constexpr int S0 = 1; static constexpr bool W = true, FH = true, G = true; };
-template <> struct Cfg<24, double> { static constexpr int S0 = 2; static constexpr bool W = true, FH = false, G = false; };
-template <> struct Cfg<32, double> { static constexpr int S0 = 4; static constexpr bool W = true, FH = false, G = false; };
-template <> struct Cfg<16, float> { static constexpr int S0 = 1; static constexpr bool W = true, FH = true, G = true; };
-template <> struct Cfg<24, float> { static constexpr int S0 = 1; static constexpr bool W = true, FH = true, G = true; };
-template <> struct Cfg<32, float> { static constexpr int S0 = 2; static constexpr bool W = true, FH = false, G = false; };
-template <> struct Cfg<48, float> { static constexpr int S0 = 4; static constexpr bool W = true, FH = false, G = false; };
-template <> struct Cfg<64, float> { static constexpr int S0 = 1; static constexpr bool W = false, FH = false, G = false; };
+#define COLL_CFG(N_, T_, S0_, W_, FH_, G_, PAD_)                                          \
+  template <> struct Cfg<N_, T_> {                                                         \
+    static constexpr int S0 = S0_;                                                         \
+    static constexpr bool W = W_, FH = FH_, G = G_, FH_PAD = PAD_;                         \
+  };
+//        N   T       S0  W     Fh     G      Fh padded
+COLL_CFG(16, double,  1, true, true,  true,  true)
+COLL_CFG(24, double,  2, true, false, true,  true)
+COLL_CFG(32, double,  4, true, false, true,  true)
+COLL_CFG(16, df,      1, true, true,  true,  true)
+COLL_CFG(24, df,      2, true, false, true,  true)
+COLL_CFG(32, df,      4, true, false, true,  true)
+COLL_CFG(16, float,   1, true, true,  true,  true)
+COLL_CFG(24, float,   1, true, true,  true,  true)
+COLL_CFG(32, float,   4, true, true,  true,  false)
+COLL_CFG(48, float,   8, true, false, true,  true)
+COLL_CFG(64, float,  16, true, false, true,  true)
+#undef COLL_CFG
 
 constexpr int kThreads = 256;
 
 template <int N, typename T> struct Lay {
   using Cf = Cfg<N, T>;
   static constexpr int H = N / 2;
-  static constexpr int FH_ROW = H + 1;
+  static constexpr int FH_ROW = Cf::FH_PAD ? H + 1 : H;
   static constexpr int W_ROW = N + 1;
   static constexpr int S0 = Cf::S0;
   static constexpr int NS = N / S0;
   static constexpr size_t W_BYTES = size_t(NS) * N * W_ROW * 2 * sizeof(T);
   static constexpr size_t FH_BYTES = size_t(N) * N * FH_ROW * 2 * sizeof(T);
-  static constexpr size_t G_BYTES = size_t(N) * N * N * sizeof(T);
+  static constexpr size_t G_BYTES = size_t(NS) * N * N * sizeof(T);        // one slab
   static constexpr size_t round16(size_t b) { return (b + 15) / 16 * 16; }
   static constexpr size_t SMEM = (Cf::W ? round16(W_BYTES) : 0) + (Cf::FH ? round16(FH_BYTES) : 0) +
                                  (Cf::G ? round16(G_BYTES) : 0);
   static constexpr size_t WS = (Cf::W ? 0 : round16(W_BYTES)) + (Cf::FH ? 0 : round16(FH_BYTES)) +
                                (Cf::G ? 0 : round16(G_BYTES));
+  static_assert(SMEM <= 232448, "shared-memory layout exceeds 227 KB");
+  static_assert(N % S0 == 0, "S0 must divide N");
 };
 
 }  // namespace coll

@@ -12,6 +12,7 @@
 // SIGN = +1: inverse transform  x_j = sum_k X_k exp(+2 pi i jk / L)  (unnormalised)
 #pragma once
 
+#include "dfloat.cuh"
 #include "twiddles.h"
 
 namespace coll {
@@ -25,6 +26,13 @@ template <> struct Tw<float> {
   static __device__ __forceinline__ float c(int n) { return kTwCosF[n]; }
   static __device__ __forceinline__ float s(int n) { return kTwSinF[n]; }
 };
+template <> struct Tw<df> {
+  static __device__ __forceinline__ df c(int n) { return df{kTwCosF[n], kTwCosL[n]}; }
+  static __device__ __forceinline__ df s(int n) { return df{kTwSinF[n], kTwSinL[n]}; }
+};
+
+__device__ __forceinline__ double half(double x) { return 0.5 * x; }
+__device__ __forceinline__ float half(float x) { return 0.5f * x; }
 
 // first radix applied to a sub-transform of length L
 __host__ __device__ constexpr int radix_of(int L) {
@@ -85,7 +93,7 @@ __device__ __forceinline__ void butterfly(T* xr, T* xi) {
     const T h = Tw<T>::s(64);                 // sin(2 pi / 3) = sqrt(3)/2
     T tr = xr[1] + xr[2], ti = xi[1] + xi[2];
     T ur = xr[1] - xr[2], ui = xi[1] - xi[2];
-    T mr = xr[0] - T(0.5) * tr, mi = xi[0] - T(0.5) * ti;
+    T mr = xr[0] - half(tr), mi = xi[0] - half(ti);
     // v = SIGN i h u
     T vr = SIGN > 0 ? -h * ui : h * ui;
     T vi = SIGN > 0 ? h * ur : -h * ur;

@@ -1,4 +1,5 @@
-"""Writes twiddles.h: cos and sin of 2 pi n / 192, n = 0..191, correctly rounded.
+"""Writes twiddles.h: cos and sin of 2 pi n / 192, n = 0..191, correctly rounded
+(double; float; and float tails for float-pair arithmetic).
 
 192 = lcm(16, 24, 32, 48, 64), so every twiddle of the supported FFT lengths
 and of their radix-2/3/4 sub-lengths is an entry of this table.  Values are
@@ -11,7 +12,7 @@ import mpmath
 import numpy as np
 
 mpmath.mp.dps = 50
-rows_d, rows_f = [], []
+rows_d, rows_f, rows_l = [], [], []
 for n in range(192):
     a = 2 * mpmath.pi * n / 192
     c, s = mpmath.cos(a), mpmath.sin(a)
@@ -20,6 +21,10 @@ for n in range(192):
     sf = float(np.float32(mpmath.nstr(s, 40)))
     rows_d.append((cd.hex(), sd.hex()))
     rows_f.append((cf.hex(), sf.hex()))
+    # tails of the float-pair twiddles: the float nearest to (exact - head)
+    cl = float(np.float32(mpmath.nstr(c - mpmath.mpf(cf), 40)))
+    sl = float(np.float32(mpmath.nstr(s - mpmath.mpf(sf), 40)))
+    rows_l.append((cl.hex(), sl.hex()))
 out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "twiddles.h")
 with open(out, "w") as fh:
     fh.write("// Generated by gen_twiddles.py: cos/sin(2 pi n / 192), correctly rounded.\n")
@@ -32,3 +37,8 @@ with open(out, "w") as fh:
     fh.write(",\n".join("  %sf" % c for c, _ in rows_f) + "};\n")
     fh.write("static __constant__ float kTwSinF[192] = {\n")
     fh.write(",\n".join("  %sf" % s for _, s in rows_f) + "};\n")
+    fh.write("// tails: cos - kTwCosF and sin - kTwSinF rounded to float (float-pair twiddles)\n")
+    fh.write("static __constant__ float kTwCosL[192] = {\n")
+    fh.write(",\n".join("  %sf" % c for c, _ in rows_l) + "};\n")
+    fh.write("static __constant__ float kTwSinL[192] = {\n")
+    fh.write(",\n".join("  %sf" % s for _, s in rows_l) + "};\n")

@@ -72,6 +72,6 @@ extern "C" coll_status coll_eval_batch_static(coll_plan p, const void* f, void* 
   a.ws = ws;
   a.ws_per_cta = per_cta;
   a.status = p->status_dev;
-  const int e = coll::launch_collision(p->d.N, p->f64, p->io_f64, a, int(grid), stream);
+  const int e = coll::launch_collision(p->d.N, p->ctype, p->io_f64, a, int(grid), stream);
   return e == 0 ? COLL_OK : COLL_ECUDA;
 }
