@@ -164,12 +164,18 @@ coll_status coll_eval_batch_static(coll_plan plan, const void* f, void* Q, int64
                                    coll_stream stream);
 
 /*
- * Ragged batch: n_groups groups, each with its own plan (different N and/or
- * precision), its own f and Q arrays and cells_per_group[g] cells, evaluated
- * in ONE persistent launch that schedules the largest cells first.  All plans
- * must live on the current device and share the same precision class
- * (COLL_F32 or COLL_F64 for every group).  ws must hold at least
- * coll_ragged_workspace_size() bytes for the same groups.
+ * Ragged batch: n_groups (1 .. 32) groups, each with its own plan (its own N,
+ * lambda, quadrature), its own f and Q arrays and cells_per_group[g] cells,
+ * evaluated in ONE persistent launch: CTAs take cells from a device counter,
+ * groups ordered by decreasing N so the largest cells start first.  Every
+ * plan must live on the current device and use the same compute type, with
+ * the io type that goes with it (COLL_F32: float io; COLL_F64 and COLL_F32X2:
+ * double io); otherwise COLL_EUNSUPPORTED.  Results are bitwise identical to
+ * coll_eval_batch of each group alone (same per-cell code and order of
+ * operations).  ws (256-byte aligned) must hold coll_ragged_workspace_size()
+ * bytes for the same groups; its first 256 bytes hold the work counter, reset
+ * by an async memset on the stream before the launch (both capture into a
+ * CUDA graph).
  */
 typedef struct {
   coll_plan plan;

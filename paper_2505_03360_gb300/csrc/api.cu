@@ -35,6 +35,60 @@ int grid_for(const coll_plan_s* p, long long n_cells) {
   return int(g);
 }
 
+// Validate a ragged request and build its launch table: groups sorted by
+// decreasing N (largest cells scheduled first), prefix sums of cell counts.
+coll_status ragged_prepare(const coll_cell_group* groups, const int64_t* cells, int32_t n, RaggedTable* t,
+                           int* ctype, int* grid, size_t* ws_per_cta, size_t* total_bytes) {
+  if (!groups || !cells || n <= 0 || n > kMaxRaggedGroups) return COLL_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return COLL_ECUDA;
+  const coll_plan_s* p0 = groups[0].plan;
+  if (!p0) return COLL_EINVAL;
+  *ctype = p0->ctype;
+  const bool want_io_f64 = p0->ctype != kCF32;
+  int order[kMaxRaggedGroups];
+  for (int i = 0; i < n; ++i) {
+    const coll_plan_s* p = groups[i].plan;
+    if (!p || p->device != dev || cells[i] < 0) return COLL_EINVAL;
+    if (p->ctype != *ctype) return COLL_EUNSUPPORTED;
+    if (p->io_f64 != want_io_f64) return COLL_EUNSUPPORTED;
+    if (cells[i] > 0 && (!groups[i].f || !groups[i].Q || groups[i].f == groups[i].Q)) return COLL_EINVAL;
+    order[i] = i;
+  }
+  for (int i = 1; i < n; ++i)                       // stable insertion sort, N descending
+    for (int j = i; j > 0 && groups[order[j]].plan->d.N > groups[order[j - 1]].plan->d.N; --j) {
+      const int tmp = order[j];
+      order[j] = order[j - 1];
+      order[j - 1] = tmp;
+    }
+  long long acc = 0;
+  t->n_items = n;
+  for (int k = 0; k < n; ++k) {
+    const coll_cell_group& g = groups[order[k]];
+    RaggedItem& it = t->items[k];
+    it.f = g.f;
+    it.Q = g.Q;
+    it.tab = g.plan->tab_dev;
+    it.n_cells = cells[order[k]];
+    it.first_unit = acc;
+    it.status = g.plan->status_dev;
+    it.N = g.plan->d.N;
+    it.n_terms = g.plan->n_terms;
+    acc += it.n_cells;
+  }
+  t->total_units = acc;
+  int per = 0;
+  if (ragged_max_ctas_per_sm(*ctype, &per) != 0 || per < 1) return COLL_ECUDA;
+  size_t smem = 0;
+  if (ragged_layout(*ctype, &smem, ws_per_cta) != 0) return COLL_ECUDA;
+  long long g = static_cast<long long>(p0->num_sms) * per;
+  if (g > acc) g = acc;
+  if (g < 1) g = 1;
+  *grid = int(g);
+  *total_bytes = 256 + size_t(g) * (*ws_per_cta);
+  return COLL_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -209,22 +263,29 @@ coll_status coll_device_status_clear(coll_plan p) {
 
 coll_status coll_ragged_workspace_size(const coll_cell_group* groups, const int64_t* cells_per_group,
                                        int32_t n_groups, size_t* bytes) {
-  (void)groups;
-  (void)cells_per_group;
-  (void)n_groups;
-  (void)bytes;
-  return COLL_EUNSUPPORTED;
+  if (!bytes) return COLL_EINVAL;
+  RaggedTable t;
+  int ctype = 0, grid = 0;
+  size_t wsper = 0, total = 0;
+  const coll_status st = ragged_prepare(groups, cells_per_group, n_groups, &t, &ctype, &grid, &wsper, &total);
+  if (st != COLL_OK) return st;
+  *bytes = total;
+  return COLL_OK;
 }
 
 coll_status coll_eval_ragged(const coll_cell_group* groups, const int64_t* cells_per_group, int32_t n_groups,
                              void* ws, size_t ws_bytes, coll_stream stream) {
-  (void)groups;
-  (void)cells_per_group;
-  (void)n_groups;
-  (void)ws;
-  (void)ws_bytes;
-  (void)stream;
-  return COLL_EUNSUPPORTED;
+  RaggedTable t;
+  int ctype = 0, grid = 0;
+  size_t wsper = 0, total = 0;
+  const coll_status st = ragged_prepare(groups, cells_per_group, n_groups, &t, &ctype, &grid, &wsper, &total);
+  if (st != COLL_OK) return st;
+  if (t.total_units == 0) return COLL_OK;
+  if (!ws || !aligned256(ws)) return COLL_EINVAL;
+  if (ws_bytes < total) return COLL_ENOMEM;
+  if (cudaMemsetAsync(ws, 0, 256, static_cast<cudaStream_t>(stream)) != cudaSuccess) return COLL_ECUDA;
+  const int e = launch_ragged(ctype, t, ws, wsper, grid, stream);
+  return e == 0 ? COLL_OK : COLL_ECUDA;
 }
 
 }  // extern "C"

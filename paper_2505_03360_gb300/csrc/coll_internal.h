@@ -62,22 +62,28 @@ enum : int { kStatusNonFinite = 1, kStatusTimeout = 2 };
 int launch_collision(int N, int ctype, bool io_f64, const CollArgs& a, int grid, void* stream);
 int collision_max_ctas_per_sm(int N, int ctype, bool io_f64, int* ctas);
 
-// Ragged launch: one persistent kernel over mixed N (collision.cu).
-struct RaggedItem {            // one group of cells with the same plan
+// Ragged launch: one persistent kernel over groups of cells with mixed N
+// (ragged_*.cu).  Groups are passed by value in the kernel parameters.
+constexpr int kMaxRaggedGroups = 32;
+struct RaggedItem {            // one group of cells evaluated with one plan
   const void* f;
   void* Q;
   const void* tab;
   long long n_cells;
-  long long first_unit;       // prefix sum of n_cells in schedule order
+  long long first_unit;        // prefix sum of n_cells in schedule order
+  int* status;
   int N;
   int n_terms;
-  int io_f64;
-  int* status;
 };
-int launch_ragged(bool f64, const RaggedItem* items_dev, int n_items, long long total_cells,
-                  void* ws, size_t ws_per_cta, int* counter_dev, int grid, void* stream);
-int ragged_layout(bool f64, size_t* smem_bytes, size_t* ws_per_cta, int* threads);
-int ragged_max_ctas_per_sm(bool f64, int* ctas);
+struct RaggedTable {
+  RaggedItem items[kMaxRaggedGroups];
+  int n_items;
+  long long total_units;
+};
+// ctype: kCF32 (float io) or kCF64 / kCDF (double io)
+int launch_ragged(int ctype, const RaggedTable& t, void* ws, size_t ws_per_cta, int grid, void* stream);
+int ragged_layout(int ctype, size_t* smem_bytes, size_t* ws_per_cta);
+int ragged_max_ctas_per_sm(int ctype, int* ctas);
 
 // Moments kernel (moments.cu)
 int launch_moments(const void* f, int io_f64, int N, double L, long long n_cells, double eta0,

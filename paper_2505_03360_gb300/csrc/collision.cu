@@ -103,6 +103,48 @@ bool layout_info(int N, int ctype, LayoutInfo* out) {
   }                                                                                         \
   return int(cudaErrorInvalidValue);
 
+int ragged_launch_f32(const RaggedTable& t, void* ws, size_t ws_per_cta, int grid, cudaStream_t st);
+int ragged_launch_f64(const RaggedTable& t, void* ws, size_t ws_per_cta, int grid, cudaStream_t st);
+int ragged_launch_x(const RaggedTable& t, void* ws, size_t ws_per_cta, int grid, cudaStream_t st);
+int ragged_occupancy_f32(int* ctas);
+int ragged_occupancy_f64(int* ctas);
+int ragged_occupancy_x(int* ctas);
+size_t ragged_smem_f32();
+size_t ragged_smem_f64();
+size_t ragged_smem_x();
+size_t ragged_ws_f32();
+size_t ragged_ws_f64();
+size_t ragged_ws_x();
+
+int launch_ragged(int ctype, const RaggedTable& t, void* ws, size_t ws_per_cta, int grid, void* stream) {
+  count_launches(1);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  switch (ctype) {
+    case kCF32: return ragged_launch_f32(t, ws, ws_per_cta, grid, st);
+    case kCF64: return ragged_launch_f64(t, ws, ws_per_cta, grid, st);
+    case kCDF: return ragged_launch_x(t, ws, ws_per_cta, grid, st);
+  }
+  return int(cudaErrorInvalidValue);
+}
+
+int ragged_layout(int ctype, size_t* smem_bytes, size_t* ws_per_cta) {
+  switch (ctype) {
+    case kCF32: *smem_bytes = ragged_smem_f32(); *ws_per_cta = ragged_ws_f32(); return 0;
+    case kCF64: *smem_bytes = ragged_smem_f64(); *ws_per_cta = ragged_ws_f64(); return 0;
+    case kCDF: *smem_bytes = ragged_smem_x(); *ws_per_cta = ragged_ws_x(); return 0;
+  }
+  return int(cudaErrorInvalidValue);
+}
+
+int ragged_max_ctas_per_sm(int ctype, int* ctas) {
+  switch (ctype) {
+    case kCF32: return ragged_occupancy_f32(ctas);
+    case kCF64: return ragged_occupancy_f64(ctas);
+    case kCDF: return ragged_occupancy_x(ctas);
+  }
+  return int(cudaErrorInvalidValue);
+}
+
 int launch_collision(int N, int ctype, bool io_f64, const CollArgs& a, int grid, void* stream) {
   count_launches(1);
   cudaStream_t st = static_cast<cudaStream_t>(stream);

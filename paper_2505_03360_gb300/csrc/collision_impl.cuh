@@ -29,6 +29,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <initializer_list>
+
 #include "coll_internal.h"
 #include "collision_layout.cuh"
 #include "fft.cuh"
@@ -100,7 +102,7 @@ __device__ __noinline__ bool run_pass(int mode, typename C2<T>::type* base, int 
 #pragma unroll
       for (int j = 0; j < N; ++j) p[size_t(j) * s_elem] = V2{xr[j], (mode == kPassFwd) ? -xi[j] : xi[j]};
     } else {
-      T* g = G + (size_t(a) * N + b) * N;
+      T* g = G + (size_t(a) * N + b) * (N + 1);          // padded rows: conflict-free row access
       if (!last) {
 #pragma unroll
         for (int j = 0; j < N; ++j) g[j] += xr[j] * xi[j];
@@ -206,7 +208,7 @@ __device__ __forceinline__ void process_cell(const Tio* __restrict__ f, Tio* __r
   __syncthreads();
 
   for (int s = 0; s < S0; ++s) {
-    for (int i = threadIdx.x; i < NS * N * N; i += kThreads) G[i] = T{};
+    for (int i = threadIdx.x; i < NS * N * (N + 1); i += kThreads) G[i] = T{};
     __syncthreads();
     for (int t = 0; t < n_terms; ++t) {
       run_p1<N, T>(tab + size_t(t) * N * N * H, Fh, W, s);
@@ -233,6 +235,81 @@ __global__ void __launch_bounds__(kThreads, 1) collision_kernel(CollArgs a) {
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.status, kStatusNonFinite);
 }
+
+// Persistent kernel over a ragged table of cell groups (mixed N): CTAs take
+// cells from a global counter in schedule order (the host sorts the groups by
+// decreasing N, largest work first); each cell runs the per-N body above.
+template <typename T, typename Tio, int... Ns>
+struct RaggedDispatch;
+
+template <typename T, typename Tio>
+struct RaggedDispatch<T, Tio> {
+  static __device__ __forceinline__ void run(int, const Tio*, Tio*, const typename C2<T>::type*, int, unsigned char*,
+                                             unsigned char*, bool&) {}
+};
+
+template <typename T, typename Tio, int N0, int... Ns>
+struct RaggedDispatch<T, Tio, N0, Ns...> {
+  static __device__ __forceinline__ void run(int N, const Tio* f, Tio* Q, const typename C2<T>::type* tab, int nt,
+                                             unsigned char* smem, unsigned char* wsc, bool& bad) {
+    if (N == N0) process_cell<N0, T, Tio>(f, Q, tab, nt, smem, wsc, bad);
+    else RaggedDispatch<T, Tio, Ns...>::run(N, f, Q, tab, nt, smem, wsc, bad);
+  }
+};
+
+template <typename T, typename Tio, int... Ns>
+__global__ void __launch_bounds__(kThreads, 1) ragged_kernel(RaggedTable tbl, void* ws, size_t ws_per_cta) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  // the whole dynamic shared memory may be in use by the largest N, so the
+  // work-unit broadcast goes through a 256-byte header of the CTA's workspace
+  unsigned long long* counter = static_cast<unsigned long long*>(ws);
+  unsigned char* slice = static_cast<unsigned char*>(ws) + 256 + size_t(blockIdx.x) * ws_per_cta;
+  volatile long long* unit_slot = reinterpret_cast<volatile long long*>(slice);
+  unsigned char* wsc = slice + 256;
+  for (;;) {
+    if (threadIdx.x == 0) *unit_slot = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const long long u = *unit_slot;
+    __syncthreads();
+    if (u >= tbl.total_units) break;
+    int g = 0;
+    while (g + 1 < tbl.n_items && u >= tbl.items[g + 1].first_unit) ++g;
+    const RaggedItem& it = tbl.items[g];
+    const long long c = u - it.first_unit;
+    const size_t n3 = size_t(it.N) * it.N * it.N;
+    bool bad = false;
+    RaggedDispatch<T, Tio, Ns...>::run(it.N, static_cast<const Tio*>(it.f) + c * n3, static_cast<Tio*>(it.Q) + c * n3,
+                                       static_cast<const typename C2<T>::type*>(it.tab), it.n_terms, smem, wsc, bad);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(it.status, kStatusNonFinite);
+  }
+}
+
+template <typename T, typename Tio, int... Ns>
+struct RaggedLaunch {
+  static constexpr size_t smem() {
+    size_t m = 0;
+    for (size_t v : {Lay<Ns, T>::SMEM...}) m = v > m ? v : m;
+    return m;
+  }
+  static constexpr size_t ws() {        // per CTA: 256-byte header + the largest scratch
+    size_t m = 0;
+    for (size_t v : {Lay<Ns, T>::WS...}) m = v > m ? v : m;
+    return 256 + (m + 255) / 256 * 256;
+  }
+  static int launch(const RaggedTable& t, void* wsp, size_t ws_per_cta, int grid, cudaStream_t st) {
+    auto k = ragged_kernel<T, Tio, Ns...>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
+    if (e != cudaSuccess) return int(e);
+    k<<<grid, kThreads, smem(), st>>>(t, wsp, ws_per_cta);
+    return int(cudaGetLastError());
+  }
+  static int occupancy(int* ctas) {
+    auto k = ragged_kernel<T, Tio, Ns...>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
+    if (e != cudaSuccess) return int(e);
+    return int(cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k, kThreads, smem()));
+  }
+};
 
 template <int N, typename T, typename Tio>
 int launch_one(const CollArgs& a, int grid, cudaStream_t st) {

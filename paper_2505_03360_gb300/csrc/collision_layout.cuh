@@ -30,7 +30,7 @@ COLL_CFG(16, df,      1, true, true,  true,  true)
 COLL_CFG(24, df,      2, true, false, true,  true)
 COLL_CFG(32, df,      4, true, false, true,  true)
 COLL_CFG(16, float,   1, true, true,  true,  true)
-COLL_CFG(24, float,   1, true, true,  true,  true)
+COLL_CFG(24, float,   1, true, true,  true,  false)
 COLL_CFG(32, float,   4, true, true,  true,  false)
 COLL_CFG(48, float,   8, true, false, true,  true)
 COLL_CFG(64, float,  16, true, false, true,  true)
@@ -43,11 +43,12 @@ template <int N, typename T> struct Lay {
   static constexpr int H = N / 2;
   static constexpr int FH_ROW = Cf::FH_PAD ? H + 1 : H;
   static constexpr int W_ROW = N + 1;
+  static constexpr int G_ROW = N + 1;                                       // padded gain rows
   static constexpr int S0 = Cf::S0;
   static constexpr int NS = N / S0;
   static constexpr size_t W_BYTES = size_t(NS) * N * W_ROW * 2 * sizeof(T);
   static constexpr size_t FH_BYTES = size_t(N) * N * FH_ROW * 2 * sizeof(T);
-  static constexpr size_t G_BYTES = size_t(NS) * N * N * sizeof(T);        // one slab
+  static constexpr size_t G_BYTES = size_t(NS) * N * G_ROW * sizeof(T);    // one slab
   static constexpr size_t round16(size_t b) { return (b + 15) / 16 * 16; }
   static constexpr size_t SMEM = (Cf::W ? round16(W_BYTES) : 0) + (Cf::FH ? round16(FH_BYTES) : 0) +
                                  (Cf::G ? round16(G_BYTES) : 0);

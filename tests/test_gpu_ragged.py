@@ -1,0 +1,109 @@
+"""Ragged persistent launch (mixed N in one kernel) and CUDA-graph replay,
+through the C ABI.  Results must equal the per-group coll_eval_batch results
+bitwise (same per-cell code), and sampled cells must match the oracle within
+the precision's tolerance."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_2505_03360_gb300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_2505_03360_gb300 import coll, synth  # noqa: E402
+from oracle.collision import q_fast  # noqa: E402
+from oracle.kernel import Params, multipliers  # noqa: E402
+
+L = synth.DEFAULT_L
+TOL = {"f64": 1e-12, "f32": 5e-4, "f32x2": 1e-10}
+
+
+def _groups(prec, Ns, counts, seed=0):
+    plans, fs, Qs = [], [], []
+    dt = torch.float32 if prec == "f32" else torch.float64
+    r = synth.rng(seed)
+    for N, n in zip(Ns, counts):
+        plan = coll.Plan(N, L, lam=1.0, M=32, Mtheta=4, Mr=8, prec=prec, max_cells=max(n, 1))
+        cells = np.stack([synth.anisotropic_cell(N, L, r, dtype=np.float64) for _ in range(n)]) if n else \
+            np.zeros((0, N, N, N))
+        fs.append(torch.from_numpy(cells).to("cuda", dt))
+        Qs.append(torch.full_like(fs[-1], float("nan")))
+        plans.append(plan)
+    return plans, fs, Qs
+
+
+@pytest.mark.parametrize("prec,Ns,counts", [
+    ("f32", [16, 48, 24, 32, 64], [5, 2, 4, 3, 1]),
+    ("f64", [24, 16, 32], [3, 6, 2]),
+    ("f32x2", [32, 16, 24], [2, 4, 3]),
+])
+def test_ragged_equals_per_group_and_oracle(prec, Ns, counts):
+    plans, fs, Qs = _groups(prec, Ns, counts, seed=len(Ns))
+    groups = [(p.handle, f, Q) for p, f, Q in zip(plans, fs, Qs)]
+    nb = coll.coll_ragged_workspace_size(groups, counts)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    coll.coll_eval_ragged(groups, counts, ws)
+    torch.cuda.synchronize()
+    for p, f, Q, N, n in zip(plans, fs, Qs, Ns, counts):
+        assert p.status() == coll.COLL_OK
+        ref = p.eval(f)
+        torch.cuda.synchronize()
+        assert torch.equal(Q, ref), N
+        pr = Params(N=N, L=L, lam=1.0, M=32, Mtheta=4, Mr=8)
+        m = multipliers(pr)
+        c = n - 1
+        want = q_fast(f[c].double().cpu().numpy(), pr, m)
+        got = Q[c].double().cpu().numpy()
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) <= TOL[prec], N
+    for p in plans:
+        p.close()
+
+
+def test_ragged_cuda_graph_replay():
+    """Memset + persistent launch captured in a CUDA graph; two replays equal eager."""
+    Ns, counts = [16, 32, 24], [6, 3, 4]
+    plans, fs, Qs = _groups("f32", Ns, counts, seed=9)
+    groups = [(p.handle, f, Q) for p, f, Q in zip(plans, fs, Qs)]
+    ws = torch.empty(coll.coll_ragged_workspace_size(groups, counts), dtype=torch.uint8, device="cuda")
+    coll.coll_eval_ragged(groups, counts, ws)
+    torch.cuda.synchronize()
+    eager = [Q.clone() for Q in Qs]
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        for Q in Qs:
+            Q.fill_(float("nan"))
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            coll.coll_eval_ragged(groups, counts, ws, stream=s)
+    for _ in range(2):
+        for Q in Qs:
+            Q.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        for Q, E in zip(Qs, eager):
+            assert torch.equal(Q, E)
+    for p in plans:
+        p.close()
+
+
+def test_ragged_errors():
+    p32 = coll.Plan(16, L, lam=1.0, M=32, Mtheta=4, Mr=8, prec="f32", max_cells=1)
+    p64 = coll.Plan(16, L, lam=1.0, M=32, Mtheta=4, Mr=8, prec="f64", max_cells=1)
+    f32 = torch.zeros((1, 16, 16, 16), dtype=torch.float32, device="cuda")
+    f64 = torch.zeros((1, 16, 16, 16), dtype=torch.float64, device="cuda")
+    with pytest.raises(coll.CollError) as e:                   # mixed compute types
+        coll.coll_ragged_workspace_size([(p32.handle, f32, torch.empty_like(f32)),
+                                         (p64.handle, f64, torch.empty_like(f64))], [1, 1])
+    assert e.value.status == coll.COLL_EUNSUPPORTED
+    with pytest.raises(coll.CollError) as e:                   # aliasing f and Q
+        coll.coll_ragged_workspace_size([(p32.handle, f32, f32)], [1])
+    assert e.value.status == coll.COLL_EINVAL
+    ok = [(p32.handle, f32, torch.empty_like(f32))]
+    ws = torch.empty(coll.coll_ragged_workspace_size(ok, [1]), dtype=torch.uint8, device="cuda")
+    assert coll.coll_eval_ragged(ok, [1], ws[:128], check=False) == coll.COLL_ENOMEM
+    assert coll.coll_eval_ragged(ok, [0], ws, check=False) == coll.COLL_OK
+    p32.close()
+    p64.close()
