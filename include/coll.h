@@ -140,6 +140,21 @@ coll_status coll_eval_batch(coll_plan plan, const void* f, void* Q, int64_t n_ce
                             void* ws, size_t ws_bytes, coll_stream stream);
 
 /*
+ * Autotuner: the fused kernel has two slab shapes per (N, precision) (how
+ * many v0-slabs the axis-0 inverse pass is split into, and which arrays stay
+ * in shared memory).  coll_plan_autotune times each on the caller's batch
+ * (one warm-up and two timed evaluations each, on `stream`; the call
+ * synchronises) and stores the faster one in the plan; *chosen (may be NULL)
+ * receives it.  Q is overwritten.  ws must hold coll_workspace_size(plan,
+ * n_cells) bytes, which covers every shape.  Results of both shapes agree to
+ * rounding (the same operations in a different order of slabs).
+ * coll_plan_set_variant selects a shape directly (0 or 1).
+ */
+coll_status coll_plan_autotune(coll_plan plan, const void* f, void* Q, int64_t n_cells, void* ws,
+                               size_t ws_bytes, coll_stream stream, int32_t* chosen);
+coll_status coll_plan_set_variant(coll_plan plan, int32_t variant);
+
+/*
  * coll_eval_batch_static -- coll_eval_batch without a caller-provided
  * workspace, for callers that cannot allocate device memory: code that runs
  * while a CUDA graph is being captured (cudaMalloc is not allowed there),

@@ -57,6 +57,8 @@ def _load():
         "coll_workspace_size": (I32, [P, I64, ctypes.POINTER(SZ)]),
         "coll_eval_batch": (I32, [P, P, P, I64, P, SZ, P]),
         "coll_eval_batch_static": (I32, [P, P, P, I64, P]),
+        "coll_plan_autotune": (I32, [P, P, P, I64, P, SZ, P, ctypes.POINTER(I32)]),
+        "coll_plan_set_variant": (I32, [P, I32]),
         "coll_ragged_workspace_size": (I32, [ctypes.POINTER(coll_cell_group), ctypes.POINTER(I64), I32,
                                              ctypes.POINTER(SZ)]),
         "coll_eval_ragged": (I32, [ctypes.POINTER(coll_cell_group), ctypes.POINTER(I64), I32, P, SZ, P]),
@@ -158,6 +160,19 @@ def coll_eval_batch_static(plan: int, f, Q, n_cells: int, stream=None, check=Tru
     return st
 
 
+def coll_plan_autotune(plan: int, f, Q, n_cells: int, ws, stream=None) -> int:
+    """Time every slab-shape variant on this batch; the faster is kept in the plan."""
+    ch = ctypes.c_int32(-1)
+    _check(_lib.coll_plan_autotune(ctypes.c_void_p(plan), _ptr(f), _ptr(Q), int(n_cells), _ptr(ws),
+                                   ws.numel() * ws.element_size(), _stream_ptr(stream), ctypes.byref(ch)),
+           "coll_plan_autotune")
+    return ch.value
+
+
+def coll_plan_set_variant(plan: int, variant: int):
+    _check(_lib.coll_plan_set_variant(ctypes.c_void_p(plan), int(variant)), "coll_plan_set_variant")
+
+
 def coll_ragged_workspace_size(groups, cells) -> int:
     arr, cnt = _groups(groups, cells)
     b = ctypes.c_size_t()
@@ -253,6 +268,12 @@ class Plan:
         fd = f_host.to(self.device, non_blocking=True)
         Q = self.eval(fd, stream=stream)
         return Q.to("cpu")
+
+    def autotune(self, f, stream=None) -> int:
+        """Pick the faster slab shape on batch f (device); returns the variant."""
+        import torch
+        Q = torch.empty_like(f)
+        return coll_plan_autotune(self.handle, f, Q, f.shape[0], self.reserve(f.shape[0]), stream=stream)
 
     def status(self) -> int:
         return coll_device_status(self.handle)

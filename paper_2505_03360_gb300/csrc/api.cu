@@ -28,11 +28,21 @@ bool valid_N(int N, int ctype) {
 
 bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
 
-int grid_for(const coll_plan_s* p, long long n_cells) {
-  long long g = static_cast<long long>(p->num_sms) * p->ctas_per_sm;
+int grid_for(const coll_plan_s* p, int variant, long long n_cells) {
+  long long g = static_cast<long long>(p->num_sms) * p->ctas_per_sm[variant];
   if (g > n_cells) g = n_cells;
   if (g < 1) g = 1;
   return int(g);
+}
+
+// workspace that serves every variant (the autotuner may switch variants)
+size_t ws_need(const coll_plan_s* p, long long n_cells) {
+  size_t b = 0;
+  for (int v = 0; v < kVariants; ++v) {
+    const size_t need = size_t(grid_for(p, v, n_cells)) * p->lay[v].ws_bytes_per_cta();
+    b = need > b ? need : b;
+  }
+  return b;
 }
 
 // Validate a ragged request and build its launch table: groups sorted by
@@ -89,6 +99,27 @@ coll_status ragged_prepare(const coll_cell_group* groups, const int64_t* cells, 
   return COLL_OK;
 }
 
+coll_status eval_variant(coll_plan_s* p, int v, const void* f, void* Q, int64_t n_cells, void* ws, size_t ws_bytes,
+                         coll_stream stream) {
+  const int grid = grid_for(p, v, n_cells);
+  const size_t need = size_t(grid) * p->lay[v].ws_bytes_per_cta();
+  if (need > 0 && (!ws || !aligned256(ws))) return COLL_EINVAL;
+  if (ws_bytes < need) return COLL_ENOMEM;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return COLL_EINVAL;
+  CollArgs a;
+  a.f = f;
+  a.Q = Q;
+  a.n_cells = n_cells;
+  a.tab = p->tab_dev;
+  a.n_terms = p->n_terms;
+  a.ws = ws;
+  a.ws_per_cta = p->lay[v].ws_bytes_per_cta();
+  a.status = p->status_dev;
+  const int e = launch_collision(p->d.N, p->ctype, p->io_f64, v, a, grid, stream);
+  return e == 0 ? COLL_OK : COLL_ECUDA;
+}
+
 }  // namespace
 
 extern "C" {
@@ -135,13 +166,16 @@ coll_status coll_plan_create(const coll_plan_desc* desc, coll_plan* out) {
   p->n_terms = ht.n_terms;
   if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return COLL_ECUDA; }
   cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
-  if (!layout_info(d.N, ctype, &p->lay)) { delete p; return COLL_EUNSUPPORTED; }
-  int per = 0;
-  if (collision_max_ctas_per_sm(d.N, ctype, p->io_f64, &per) != 0 || per < 1) {
-    delete p;
-    return COLL_ECUDA;
+  p->variant = 0;
+  for (int v = 0; v < kVariants; ++v) {
+    if (!layout_info(d.N, ctype, v, &p->lay[v])) { delete p; return COLL_EUNSUPPORTED; }
+    int per = 0;
+    if (collision_max_ctas_per_sm(d.N, ctype, p->io_f64, v, &per) != 0 || per < 1) {
+      delete p;
+      return COLL_ECUDA;
+    }
+    p->ctas_per_sm[v] = per;
   }
-  p->ctas_per_sm = per;
 
   const size_t n = ht.tab.size();
   p->tab_bytes = n * (ctype == kCF32 ? sizeof(float) : sizeof(double));
@@ -206,8 +240,7 @@ coll_status coll_plan_terms(coll_plan p, int32_t* n_terms) {
 
 coll_status coll_workspace_size(coll_plan p, int64_t max_cells, size_t* bytes) {
   if (!p || !bytes || max_cells < 0) return COLL_EINVAL;
-  const long long g = max_cells == 0 ? 0 : grid_for(p, max_cells);
-  *bytes = size_t(g) * p->lay.ws_bytes_per_cta();
+  *bytes = max_cells == 0 ? 0 : ws_need(p, max_cells);
   return COLL_OK;
 }
 
@@ -216,23 +249,43 @@ coll_status coll_eval_batch(coll_plan p, const void* f, void* Q, int64_t n_cells
   if (!p || n_cells < 0) return COLL_EINVAL;
   if (n_cells == 0) return COLL_OK;
   if (!f || !Q || f == Q) return COLL_EINVAL;
-  const int grid = grid_for(p, n_cells);
-  const size_t need = size_t(grid) * p->lay.ws_bytes_per_cta();
-  if (need > 0 && (!ws || !aligned256(ws))) return COLL_EINVAL;
-  if (ws_bytes < need) return COLL_ENOMEM;
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return COLL_EINVAL;
-  CollArgs a;
-  a.f = f;
-  a.Q = Q;
-  a.n_cells = n_cells;
-  a.tab = p->tab_dev;
-  a.n_terms = p->n_terms;
-  a.ws = ws;
-  a.ws_per_cta = p->lay.ws_bytes_per_cta();
-  a.status = p->status_dev;
-  const int e = launch_collision(p->d.N, p->ctype, p->io_f64, a, grid, stream);
-  return e == 0 ? COLL_OK : COLL_ECUDA;
+  return eval_variant(p, p->variant, f, Q, n_cells, ws, ws_bytes, stream);
+}
+
+coll_status coll_plan_autotune(coll_plan p, const void* f, void* Q, int64_t n_cells, void* ws, size_t ws_bytes,
+                               coll_stream stream, int32_t* chosen) {
+  if (!p || n_cells <= 0 || !f || !Q || f == Q) return COLL_EINVAL;
+  if (ws_bytes < ws_need(p, n_cells)) return COLL_ENOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return COLL_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return COLL_ECUDA; }
+  float best = -1.0f;
+  int best_v = 0;
+  coll_status rc = COLL_OK;
+  for (int v = 0; v < kVariants && rc == COLL_OK; ++v) {
+    rc = eval_variant(p, v, f, Q, n_cells, ws, ws_bytes, stream);         // warm-up
+    if (rc != COLL_OK) break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 2 && rc == COLL_OK; ++r) rc = eval_variant(p, v, f, Q, n_cells, ws, ws_bytes, stream);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = COLL_ECUDA; break; }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best < 0.0f || ms < best) { best = ms; best_v = v; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != COLL_OK) return rc;
+  p->variant = best_v;
+  if (chosen) *chosen = best_v;
+  return COLL_OK;
+}
+
+coll_status coll_plan_set_variant(coll_plan p, int32_t variant) {
+  if (!p || variant < 0 || variant >= kVariants) return COLL_EINVAL;
+  p->variant = variant;
+  return COLL_OK;
 }
 
 coll_status moments_realizability(const void* f, int32_t io_dtype, int32_t N, double L, int64_t n_cells,

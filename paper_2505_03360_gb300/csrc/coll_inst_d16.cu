@@ -2,8 +2,12 @@
 #include "collision_impl.cuh"
 
 namespace coll {
-template int launch_one<16, double, double>(const CollArgs&, int, cudaStream_t);
-template int launch_one<16, double, float>(const CollArgs&, int, cudaStream_t);
-template int occupancy_one<16, double, double>(int*);
-template int occupancy_one<16, double, float>(int*);
+template int launch_one<16, double, double, 0>(const CollArgs&, int, cudaStream_t);
+template int launch_one<16, double, double, 1>(const CollArgs&, int, cudaStream_t);
+template int launch_one<16, double, float, 0>(const CollArgs&, int, cudaStream_t);
+template int launch_one<16, double, float, 1>(const CollArgs&, int, cudaStream_t);
+template int occupancy_one<16, double, double, 0>(int*);
+template int occupancy_one<16, double, double, 1>(int*);
+template int occupancy_one<16, double, float, 0>(int*);
+template int occupancy_one<16, double, float, 1>(int*);
 }  // namespace coll

@@ -2,8 +2,12 @@
 #include "collision_impl.cuh"
 
 namespace coll {
-template int launch_one<24, float, double>(const CollArgs&, int, cudaStream_t);
-template int launch_one<24, float, float>(const CollArgs&, int, cudaStream_t);
-template int occupancy_one<24, float, double>(int*);
-template int occupancy_one<24, float, float>(int*);
+template int launch_one<24, float, double, 0>(const CollArgs&, int, cudaStream_t);
+template int launch_one<24, float, double, 1>(const CollArgs&, int, cudaStream_t);
+template int launch_one<24, float, float, 0>(const CollArgs&, int, cudaStream_t);
+template int launch_one<24, float, float, 1>(const CollArgs&, int, cudaStream_t);
+template int occupancy_one<24, float, double, 0>(int*);
+template int occupancy_one<24, float, double, 1>(int*);
+template int occupancy_one<24, float, float, 0>(int*);
+template int occupancy_one<24, float, float, 1>(int*);
 }  // namespace coll

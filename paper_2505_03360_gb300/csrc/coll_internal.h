@@ -42,7 +42,7 @@ struct LayoutInfo {
 enum CType : int { kCF64 = 0, kCF32 = 1, kCDF = 2 };
 
 // Returns false if (N, ctype) has no kernel instantiation.
-bool layout_info(int N, int ctype, LayoutInfo* out);
+bool layout_info(int N, int ctype, int variant, LayoutInfo* out);
 
 struct CollArgs {
   const void* f;
@@ -59,8 +59,9 @@ struct CollArgs {
 enum : int { kStatusNonFinite = 1, kStatusTimeout = 2 };
 
 // Launchers (collision.cu); return cudaError_t as int.
-int launch_collision(int N, int ctype, bool io_f64, const CollArgs& a, int grid, void* stream);
-int collision_max_ctas_per_sm(int N, int ctype, bool io_f64, int* ctas);
+constexpr int kVariants = 2;   // slab-shape variants per (N, compute type), chosen by the autotuner
+int launch_collision(int N, int ctype, bool io_f64, int variant, const CollArgs& a, int grid, void* stream);
+int collision_max_ctas_per_sm(int N, int ctype, bool io_f64, int variant, int* ctas);
 
 // Ragged launch: one persistent kernel over groups of cells with mixed N
 // (ragged_*.cu).  Groups are passed by value in the kernel parameters.
@@ -109,7 +110,8 @@ struct coll_plan_s {
   void* tab_dev;     // device tables in the compute type
   size_t tab_bytes;
   int* status_dev;   // sticky status word
-  coll::LayoutInfo lay;
-  int ctas_per_sm;
+  coll::LayoutInfo lay[coll::kVariants];   // per slab-shape variant
+  int ctas_per_sm[coll::kVariants];
+  int variant;                             // chosen by coll_plan_autotune (default 0)
   int num_sms;
 };

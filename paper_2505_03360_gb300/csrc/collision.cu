@@ -8,17 +8,17 @@
 
 namespace coll {
 
-template <int N, typename T, typename Tio> int launch_one(const CollArgs& a, int grid, cudaStream_t st);
-template <int N, typename T, typename Tio> int occupancy_one(int* ctas);
+template <int N, typename T, typename Tio, int V> int launch_one(const CollArgs& a, int grid, cudaStream_t st);
+template <int N, typename T, typename Tio, int V> int occupancy_one(int* ctas);
 
-template <int N, typename T> LayoutInfo make_info() {
-  using Ly = Lay<N, T>;
+template <int N, typename T, int V> LayoutInfo make_info_v() {
+  using Ly = Lay<N, T, V>;
   LayoutInfo i;
   i.N = N;
   i.S0 = Ly::S0;
-  i.w_smem = Cfg<N, T>::W;
-  i.fh_smem = Cfg<N, T>::FH;
-  i.g_smem = Cfg<N, T>::G;
+  i.w_smem = Cfg<N, T, V>::W;
+  i.fh_smem = Cfg<N, T, V>::FH;
+  i.g_smem = Cfg<N, T, V>::G;
   i.threads = kThreads;
   i.w_bytes = Ly::round16(Ly::W_BYTES);
   i.fh_bytes = Ly::round16(Ly::FH_BYTES);
@@ -26,29 +26,33 @@ template <int N, typename T> LayoutInfo make_info() {
   return i;
 }
 
-bool layout_info(int N, int ctype, LayoutInfo* out) {
+template <int N, typename T> LayoutInfo make_info(int variant) {
+  return variant ? make_info_v<N, T, 1>() : make_info_v<N, T, 0>();
+}
+
+bool layout_info(int N, int ctype, int variant, LayoutInfo* out) {
   if (ctype == kCDF) {
     switch (N) {
-      case 16: *out = make_info<16, df>(); return true;
-      case 24: *out = make_info<24, df>(); return true;
-      case 32: *out = make_info<32, df>(); return true;
+      case 16: *out = make_info<16, df>(variant); return true;
+      case 24: *out = make_info<24, df>(variant); return true;
+      case 32: *out = make_info<32, df>(variant); return true;
       default: return false;
     }
   }
   if (ctype == kCF64) {
     switch (N) {
-      case 16: *out = make_info<16, double>(); return true;
-      case 24: *out = make_info<24, double>(); return true;
-      case 32: *out = make_info<32, double>(); return true;
+      case 16: *out = make_info<16, double>(variant); return true;
+      case 24: *out = make_info<24, double>(variant); return true;
+      case 32: *out = make_info<32, double>(variant); return true;
       default: return false;
     }
   }
   switch (N) {
-    case 16: *out = make_info<16, float>(); return true;
-    case 24: *out = make_info<24, float>(); return true;
-    case 32: *out = make_info<32, float>(); return true;
-    case 48: *out = make_info<48, float>(); return true;
-    case 64: *out = make_info<64, float>(); return true;
+    case 16: *out = make_info<16, float>(variant); return true;
+    case 24: *out = make_info<24, float>(variant); return true;
+    case 32: *out = make_info<32, float>(variant); return true;
+    case 48: *out = make_info<48, float>(variant); return true;
+    case 64: *out = make_info<64, float>(variant); return true;
     default: return false;
   }
 }
@@ -57,47 +61,47 @@ bool layout_info(int N, int ctype, LayoutInfo* out) {
   if (ctype == kCDF) {                                                                      \
     if (io_f64) {                                                                           \
       switch (N) {                                                                          \
-        case 16: return FN<16, df, double>(__VA_ARGS__);                                    \
-        case 24: return FN<24, df, double>(__VA_ARGS__);                                    \
-        case 32: return FN<32, df, double>(__VA_ARGS__);                                    \
+        case 16: return variant ? FN<16, df, double, 1>(__VA_ARGS__) : FN<16, df, double, 0>(__VA_ARGS__);                                    \
+        case 24: return variant ? FN<24, df, double, 1>(__VA_ARGS__) : FN<24, df, double, 0>(__VA_ARGS__);                                    \
+        case 32: return variant ? FN<32, df, double, 1>(__VA_ARGS__) : FN<32, df, double, 0>(__VA_ARGS__);                                    \
       }                                                                                     \
     } else {                                                                                \
       switch (N) {                                                                          \
-        case 16: return FN<16, df, float>(__VA_ARGS__);                                     \
-        case 24: return FN<24, df, float>(__VA_ARGS__);                                     \
-        case 32: return FN<32, df, float>(__VA_ARGS__);                                     \
+        case 16: return variant ? FN<16, df, float, 1>(__VA_ARGS__) : FN<16, df, float, 0>(__VA_ARGS__);                                     \
+        case 24: return variant ? FN<24, df, float, 1>(__VA_ARGS__) : FN<24, df, float, 0>(__VA_ARGS__);                                     \
+        case 32: return variant ? FN<32, df, float, 1>(__VA_ARGS__) : FN<32, df, float, 0>(__VA_ARGS__);                                     \
       }                                                                                     \
     }                                                                                       \
   } else if (ctype == kCF64) {                                                              \
     if (io_f64) {                                                                           \
       switch (N) {                                                                          \
-        case 16: return FN<16, double, double>(__VA_ARGS__);                                \
-        case 24: return FN<24, double, double>(__VA_ARGS__);                                \
-        case 32: return FN<32, double, double>(__VA_ARGS__);                                \
+        case 16: return variant ? FN<16, double, double, 1>(__VA_ARGS__) : FN<16, double, double, 0>(__VA_ARGS__);                                \
+        case 24: return variant ? FN<24, double, double, 1>(__VA_ARGS__) : FN<24, double, double, 0>(__VA_ARGS__);                                \
+        case 32: return variant ? FN<32, double, double, 1>(__VA_ARGS__) : FN<32, double, double, 0>(__VA_ARGS__);                                \
       }                                                                                     \
     } else {                                                                                \
       switch (N) {                                                                          \
-        case 16: return FN<16, double, float>(__VA_ARGS__);                                 \
-        case 24: return FN<24, double, float>(__VA_ARGS__);                                 \
-        case 32: return FN<32, double, float>(__VA_ARGS__);                                 \
+        case 16: return variant ? FN<16, double, float, 1>(__VA_ARGS__) : FN<16, double, float, 0>(__VA_ARGS__);                                 \
+        case 24: return variant ? FN<24, double, float, 1>(__VA_ARGS__) : FN<24, double, float, 0>(__VA_ARGS__);                                 \
+        case 32: return variant ? FN<32, double, float, 1>(__VA_ARGS__) : FN<32, double, float, 0>(__VA_ARGS__);                                 \
       }                                                                                     \
     }                                                                                       \
   } else {                                                                                  \
     if (io_f64) {                                                                           \
       switch (N) {                                                                          \
-        case 16: return FN<16, float, double>(__VA_ARGS__);                                 \
-        case 24: return FN<24, float, double>(__VA_ARGS__);                                 \
-        case 32: return FN<32, float, double>(__VA_ARGS__);                                 \
-        case 48: return FN<48, float, double>(__VA_ARGS__);                                 \
-        case 64: return FN<64, float, double>(__VA_ARGS__);                                 \
+        case 16: return variant ? FN<16, float, double, 1>(__VA_ARGS__) : FN<16, float, double, 0>(__VA_ARGS__);                                 \
+        case 24: return variant ? FN<24, float, double, 1>(__VA_ARGS__) : FN<24, float, double, 0>(__VA_ARGS__);                                 \
+        case 32: return variant ? FN<32, float, double, 1>(__VA_ARGS__) : FN<32, float, double, 0>(__VA_ARGS__);                                 \
+        case 48: return variant ? FN<48, float, double, 1>(__VA_ARGS__) : FN<48, float, double, 0>(__VA_ARGS__);                                 \
+        case 64: return variant ? FN<64, float, double, 1>(__VA_ARGS__) : FN<64, float, double, 0>(__VA_ARGS__);                                 \
       }                                                                                     \
     } else {                                                                                \
       switch (N) {                                                                          \
-        case 16: return FN<16, float, float>(__VA_ARGS__);                                  \
-        case 24: return FN<24, float, float>(__VA_ARGS__);                                  \
-        case 32: return FN<32, float, float>(__VA_ARGS__);                                  \
-        case 48: return FN<48, float, float>(__VA_ARGS__);                                  \
-        case 64: return FN<64, float, float>(__VA_ARGS__);                                  \
+        case 16: return variant ? FN<16, float, float, 1>(__VA_ARGS__) : FN<16, float, float, 0>(__VA_ARGS__);                                  \
+        case 24: return variant ? FN<24, float, float, 1>(__VA_ARGS__) : FN<24, float, float, 0>(__VA_ARGS__);                                  \
+        case 32: return variant ? FN<32, float, float, 1>(__VA_ARGS__) : FN<32, float, float, 0>(__VA_ARGS__);                                  \
+        case 48: return variant ? FN<48, float, float, 1>(__VA_ARGS__) : FN<48, float, float, 0>(__VA_ARGS__);                                  \
+        case 64: return variant ? FN<64, float, float, 1>(__VA_ARGS__) : FN<64, float, float, 0>(__VA_ARGS__);                                  \
       }                                                                                     \
     }                                                                                       \
   }                                                                                         \
@@ -145,13 +149,13 @@ int ragged_max_ctas_per_sm(int ctype, int* ctas) {
   return int(cudaErrorInvalidValue);
 }
 
-int launch_collision(int N, int ctype, bool io_f64, const CollArgs& a, int grid, void* stream) {
+int launch_collision(int N, int ctype, bool io_f64, int variant, const CollArgs& a, int grid, void* stream) {
   count_launches(1);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   COLL_DISPATCH(launch_one, a, grid, st)
 }
 
-int collision_max_ctas_per_sm(int N, int ctype, bool io_f64, int* ctas) {
+int collision_max_ctas_per_sm(int N, int ctype, bool io_f64, int variant, int* ctas) {
   COLL_DISPATCH(occupancy_one, ctas)
 }
 

@@ -124,10 +124,10 @@ __device__ __noinline__ bool run_pass(int mode, typename C2<T>::type* base, int 
 // P1: axis-0 inverse of (A + iB) F for every full-spectrum pencil (k1, k2),
 // forming only the outputs v0 = s + S0 m (decimation in frequency):
 //   y[k'] = w_N^{s k'} sum_q x[k' + q NS] e^{2 pi i s q / S0},  then an NS-point IFFT.
-template <int N, typename T>
+template <int N, typename T, int V>
 __device__ __noinline__ void run_p1(const typename C2<T>::type* __restrict__ tb, const typename C2<T>::type* Fh,
                                     typename C2<T>::type* W, int s) {
-  using Ly = Lay<N, T>;
+  using Ly = Lay<N, T, V>;
   using V2 = typename C2<T>::type;
   constexpr int H = Ly::H, FR = Ly::FH_ROW, WR = Ly::W_ROW, S0 = Ly::S0, NS = Ly::NS;
   for (int pid = threadIdx.x; pid < N * N; pid += kThreads) {
@@ -182,12 +182,12 @@ __device__ __noinline__ void run_p1(const typename C2<T>::type* __restrict__ tb,
 
 // ------------------------------------------------------------ per-cell body
 // smem: dynamic shared memory base; wsc: this CTA's workspace slice.
-template <int N, typename T, typename Tio>
+template <int N, typename T, typename Tio, int V = 0>
 __device__ __forceinline__ void process_cell(const Tio* __restrict__ f, Tio* __restrict__ Q,
                                              const typename C2<T>::type* __restrict__ tab, int n_terms,
                                              unsigned char* smem, unsigned char* wsc, bool& bad) {
-  using Ly = Lay<N, T>;
-  using Cf = Cfg<N, T>;
+  using Ly = Lay<N, T, V>;
+  using Cf = Cfg<N, T, V>;
   using V2 = typename C2<T>::type;
   constexpr int H = Ly::H, FR = Ly::FH_ROW, WR = Ly::W_ROW, S0 = Ly::S0, NS = Ly::NS;
 
@@ -211,7 +211,7 @@ __device__ __forceinline__ void process_cell(const Tio* __restrict__ f, Tio* __r
     for (int i = threadIdx.x; i < NS * N * (N + 1); i += kThreads) G[i] = T{};
     __syncthreads();
     for (int t = 0; t < n_terms; ++t) {
-      run_p1<N, T>(tab + size_t(t) * N * N * H, Fh, W, s);
+      run_p1<N, T, V>(tab + size_t(t) * N * N * H, Fh, W, s);
       __syncthreads();
       run_pass<N, T, Tio>(kPassInv, W, NS * N, N, N * WR, 1, WR, H, f, Q, G, s, S0, FR, false);
       __syncthreads();
@@ -222,7 +222,7 @@ __device__ __forceinline__ void process_cell(const Tio* __restrict__ f, Tio* __r
   }
 }
 
-template <int N, typename T, typename Tio>
+template <int N, typename T, typename Tio, int V>
 __global__ void __launch_bounds__(kThreads, 1) collision_kernel(CollArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* wsc = static_cast<unsigned char*>(a.ws) + size_t(blockIdx.x) * a.ws_per_cta;
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(kThreads, 1) collision_kernel(CollArgs a) {
   for (long long c = blockIdx.x; c < a.n_cells; c += gridDim.x) {
     const Tio* f = static_cast<const Tio*>(a.f) + size_t(c) * N * N * N;
     Tio* Q = static_cast<Tio*>(a.Q) + size_t(c) * N * N * N;
-    process_cell<N, T, Tio>(f, Q, tab, a.n_terms, smem, wsc, bad);
+    process_cell<N, T, Tio, V>(f, Q, tab, a.n_terms, smem, wsc, bad);
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.status, kStatusNonFinite);
 }
@@ -311,20 +311,20 @@ struct RaggedLaunch {
   }
 };
 
-template <int N, typename T, typename Tio>
+template <int N, typename T, typename Tio, int V>
 int launch_one(const CollArgs& a, int grid, cudaStream_t st) {
-  constexpr size_t smem = Lay<N, T>::SMEM;
-  auto k = collision_kernel<N, T, Tio>;
+  constexpr size_t smem = Lay<N, T, V>::SMEM;
+  auto k = collision_kernel<N, T, Tio, V>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return int(e);
   k<<<grid, kThreads, smem, st>>>(a);
   return int(cudaGetLastError());
 }
 
-template <int N, typename T, typename Tio>
+template <int N, typename T, typename Tio, int V>
 int occupancy_one(int* ctas) {
-  constexpr size_t smem = Lay<N, T>::SMEM;
-  auto k = collision_kernel<N, T, Tio>;
+  constexpr size_t smem = Lay<N, T, V>::SMEM;
+  auto k = collision_kernel<N, T, Tio, V>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return int(e);
   return int(cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k, kThreads, smem));

@@ -13,33 +13,45 @@ template <> struct C2<float> { using type = float2; };
 template <> struct C2<df> { using type = cdf; };
 
 // ----------------------------------------------------------------- layouts
-// Per (N, compute type): S0 v0-slabs; which arrays live in shared memory
-// (W = one slab of the per-term spectrum, Fh = forward half spectrum,
-// G = one slab of the gain accumulator); whether Fh rows are padded.
-template <int N, typename T> struct Cfg;
-#define COLL_CFG(N_, T_, S0_, W_, FH_, G_, PAD_)                                          \
-  template <> struct Cfg<N_, T_> {                                                         \
+// Per (N, compute type, variant V): S0 v0-slabs; which arrays live in shared
+// memory (W = one slab of the per-term spectrum, Fh = forward half spectrum,
+// G = one slab of the gain accumulator); whether Fh rows are padded.  Two
+// variants per (N, type) give the autotuner two slab shapes to choose from.
+template <int N, typename T, int V = 0> struct Cfg;
+#define COLL_CFG(N_, T_, V_, S0_, W_, FH_, G_, PAD_)                                      \
+  template <> struct Cfg<N_, T_, V_> {                                                     \
     static constexpr int S0 = S0_;                                                         \
     static constexpr bool W = W_, FH = FH_, G = G_, FH_PAD = PAD_;                         \
   };
-//        N   T       S0  W     Fh     G      Fh padded
-COLL_CFG(16, double,  1, true, true,  true,  true)
-COLL_CFG(24, double,  2, true, false, true,  true)
-COLL_CFG(32, double,  4, true, false, true,  true)
-COLL_CFG(16, df,      1, true, true,  true,  true)
-COLL_CFG(24, df,      2, true, false, true,  true)
-COLL_CFG(32, df,      4, true, false, true,  true)
-COLL_CFG(16, float,   1, true, true,  true,  true)
-COLL_CFG(24, float,   1, true, true,  true,  false)
-COLL_CFG(32, float,   4, true, true,  true,  false)
-COLL_CFG(48, float,   8, true, false, true,  true)
-COLL_CFG(64, float,  16, true, false, true,  true)
+//        N   T      V  S0  W     Fh     G      Fh padded
+COLL_CFG(16, double, 0,  1, true, true,  true,  true)
+COLL_CFG(24, double, 0,  2, true, false, true,  true)
+COLL_CFG(32, double, 0,  4, true, false, true,  true)
+COLL_CFG(16, df,     0,  1, true, true,  true,  true)
+COLL_CFG(24, df,     0,  2, true, false, true,  true)
+COLL_CFG(32, df,     0,  4, true, false, true,  true)
+COLL_CFG(16, float,  0,  1, true, true,  true,  true)
+COLL_CFG(24, float,  0,  1, true, true,  true,  false)
+COLL_CFG(32, float,  0,  4, true, true,  true,  false)
+COLL_CFG(48, float,  0,  8, true, false, true,  true)
+COLL_CFG(64, float,  0, 16, true, false, true,  true)
+COLL_CFG(16, double, 1,  2, true, true,  true,  true)
+COLL_CFG(24, double, 1,  4, true, true,  true,  true)
+COLL_CFG(32, double, 1,  8, true, false, true,  true)
+COLL_CFG(16, df,     1,  2, true, true,  true,  true)
+COLL_CFG(24, df,     1,  4, true, true,  true,  true)
+COLL_CFG(32, df,     1,  8, true, false, true,  true)
+COLL_CFG(16, float,  1,  2, true, true,  true,  true)
+COLL_CFG(24, float,  1,  2, true, true,  true,  true)
+COLL_CFG(32, float,  1,  2, true, false, true,  true)
+COLL_CFG(48, float,  1,  4, true, false, false, true)
+COLL_CFG(64, float,  1,  8, false, false, true, true)
 #undef COLL_CFG
 
 constexpr int kThreads = 256;
 
-template <int N, typename T> struct Lay {
-  using Cf = Cfg<N, T>;
+template <int N, typename T, int V = 0> struct Lay {
+  using Cf = Cfg<N, T, V>;
   static constexpr int H = N / 2;
   static constexpr int FH_ROW = Cf::FH_PAD ? H + 1 : H;
   static constexpr int W_ROW = N + 1;

@@ -53,8 +53,9 @@ extern "C" coll_status coll_eval_batch_static(coll_plan p, const void* f, void* 
   if (!f || !Q || f == Q) return COLL_EINVAL;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return COLL_EINVAL;
-  const size_t per_cta = p->lay.ws_bytes_per_cta();
-  long long grid = static_cast<long long>(p->num_sms) * p->ctas_per_sm;
+  const int v = p->variant;
+  const size_t per_cta = p->lay[v].ws_bytes_per_cta();
+  long long grid = static_cast<long long>(p->num_sms) * p->ctas_per_sm[v];
   if (grid > n_cells) grid = n_cells;
   if (per_cta > 0) {
     const long long fit = static_cast<long long>(kStaticScratchBytes / per_cta);
@@ -72,6 +73,6 @@ extern "C" coll_status coll_eval_batch_static(coll_plan p, const void* f, void* 
   a.ws = ws;
   a.ws_per_cta = per_cta;
   a.status = p->status_dev;
-  const int e = coll::launch_collision(p->d.N, p->ctype, p->io_f64, a, int(grid), stream);
+  const int e = coll::launch_collision(p->d.N, p->ctype, p->io_f64, v, a, int(grid), stream);
   return e == 0 ? COLL_OK : COLL_ECUDA;
 }

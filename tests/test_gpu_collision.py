@@ -179,3 +179,30 @@ def test_nonfinite_input_sets_sticky_status():
     coll.coll_device_status_clear(plan.handle)
     assert plan.status() == coll.COLL_OK
     plan.close()
+
+
+@pytest.mark.parametrize("prec,N", [("f64", 16), ("f64", 32), ("f32x2", 24), ("f32", 32), ("f32", 48), ("f32", 64)])
+def test_slab_shape_variants_and_autotune(prec, N):
+    """Both slab shapes match the oracle; the autotuner picks one and the plan keeps it."""
+    f = synth.bimodal_batch(3, N, L_CFG, seed=900 + N)
+    kw = dict(N=N, L=L_CFG, lam=1.0, M=32, Mtheta=4, Mr=8)
+    plan = coll.Plan(prec=prec, max_cells=3, **kw)
+    dt = torch.float64 if plan.io_dtype == 0 else torch.float32
+    fd = torch.from_numpy(f).to("cuda", dt)
+    p = Params(N=N, L=L_CFG, lam=1.0, M=32, Mtheta=4, Mr=8)
+    m = multipliers(p)
+    refs = [q_fast(fd[c].double().cpu().numpy(), p, m) for c in range(3)]
+    outs = []
+    for v in (0, 1):
+        coll.coll_plan_set_variant(plan.handle, v)
+        Q = plan.eval(fd)
+        torch.cuda.synchronize()
+        outs.append(Q.clone())
+        for c in range(3):
+            assert rel(Q[c].double().cpu().numpy(), refs[c]) <= TOL[prec], (v, c)
+    chosen = plan.autotune(fd)
+    assert chosen in (0, 1)
+    Q = plan.eval(fd)
+    torch.cuda.synchronize()
+    assert torch.equal(Q, outs[chosen])
+    plan.close()
