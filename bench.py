@@ -351,6 +351,20 @@ def run_ours(args, rank, world, local_rank):
                      "f32": {"value": n / t32, "unit": "cell-evals/s", "rel_l2_vs_f64": err32,
                              "ms_per_launch": 1e3 * t32}},
     }
+    if args.serve_requests > 0:
+        from paper_2505_03360_gb300.service import Service, stream_jobs
+        svc = Service(hbm_budget_bytes=120e9, device=str(dev))
+        svc.warm_plans()
+        jobs = stream_jobs(n_requests=args.serve_requests, rate_per_s=200.0, max_cells=args.serve_max_cells)
+        _, st = svc.run(jobs, realtime=True)
+        svc.close()
+        line["serving"] = {
+            "workload": "Poisson 200 req/s, first %d requests of the stream, cells floor(exp(U[0, ln %d])), "
+                        "N in {16,32,48,64}, lambda in {0,1}, precision in {f32, mixed}, 10 evaluations each "
+                        "(f += 1e-2 Q between), HBM budget 120 GB" % (args.serve_requests, args.serve_max_cells + 1),
+            "cell_evals_per_s": st["cell_evals_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "requests": st["requests"], "wall_s": st["wall_s"], "peak_hbm_gb": st["peak_hbm_bytes"] / 1e9,
+            "max_queue_depth": st["max_queue_depth"], "ragged_launches": st["ragged_launches"]}
     if not args.no_cpu_baseline:
         ncell = 48
         tcpu = oracle_sample(ncell)
@@ -373,6 +387,9 @@ def main():
                     help="cells per rank (default: the 4096-cell workload; smaller only for profiling)")
     ap.add_argument("--profile-only", action="store_true",
                     help="time the main path only (no e2e, no variants): for short profiler captures")
+    ap.add_argument("--serve-requests", type=int, default=100,
+                    help="requests of the serving stream measured beside the main line (0: skip)")
+    ap.add_argument("--serve-max-cells", type=int, default=64)
     ap.add_argument("--prec", default="f64", choices=["f64", "f32x2", "f32"],
                     help="compute precision of the main path in --profile-only runs")
     args = ap.parse_args()

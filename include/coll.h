@@ -179,7 +179,7 @@ coll_status coll_eval_batch_static(coll_plan plan, const void* f, void* Q, int64
                                    coll_stream stream);
 
 /*
- * Ragged batch: n_groups (1 .. 32) groups, each with its own plan (its own N,
+ * Ragged batch: n_groups (1 .. 256) groups, each with its own plan (its own N,
  * lambda, quadrature), its own f and Q arrays and cells_per_group[g] cells,
  * evaluated in ONE persistent launch: CTAs take cells from a device counter,
  * groups ordered by decreasing N so the largest cells start first.  Every
@@ -229,6 +229,14 @@ typedef struct {
 coll_status moments_realizability(const void* f, int32_t io_dtype, int32_t N, double L,
                                   int64_t n_cells, double eta0, double delta0,
                                   coll_moments* mom_out, uint8_t* mask_out, coll_stream stream);
+
+/*
+ * f <- f + dt * Q for n elements (io_dtype 0: double, 1: float), the explicit
+ * Euler step of the space-homogeneous equation df/dt = Q(f,f) (sec. 2, the
+ * kinetic equation without transport).  Device pointers, f and Q distinct;
+ * asynchronous on stream.
+ */
+coll_status coll_advance(void* f, const void* Q, int64_t n, double dt, int32_t io_dtype, coll_stream stream);
 
 /* Sticky device status of a plan (COLL_OK, COLL_ETIMEOUT, COLL_ENONFINITE);
  * synchronous: copies the word from the device.  Reading does not clear it. */

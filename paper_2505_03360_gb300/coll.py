@@ -59,6 +59,7 @@ def _load():
         "coll_eval_batch_static": (I32, [P, P, P, I64, P]),
         "coll_plan_autotune": (I32, [P, P, P, I64, P, SZ, P, ctypes.POINTER(I32)]),
         "coll_plan_set_variant": (I32, [P, I32]),
+        "coll_advance": (I32, [P, P, I64, D, I32, P]),
         "coll_ragged_workspace_size": (I32, [ctypes.POINTER(coll_cell_group), ctypes.POINTER(I64), I32,
                                              ctypes.POINTER(SZ)]),
         "coll_eval_ragged": (I32, [ctypes.POINTER(coll_cell_group), ctypes.POINTER(I64), I32, P, SZ, P]),
@@ -171,6 +172,16 @@ def coll_plan_autotune(plan: int, f, Q, n_cells: int, ws, stream=None) -> int:
 
 def coll_plan_set_variant(plan: int, variant: int):
     _check(_lib.coll_plan_set_variant(ctypes.c_void_p(plan), int(variant)), "coll_plan_set_variant")
+
+
+def coll_advance(f, Q, dt: float, stream=None, check=True) -> int:
+    """f += dt * Q on the device (same dtype, same number of elements)."""
+    import torch
+    io = 0 if f.dtype == torch.float64 else 1
+    st = _lib.coll_advance(_ptr(f), _ptr(Q), f.numel(), float(dt), io, _stream_ptr(stream))
+    if check:
+        _check(st, "coll_advance")
+    return st
 
 
 def coll_ragged_workspace_size(groups, cells) -> int:

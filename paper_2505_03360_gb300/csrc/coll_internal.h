@@ -65,7 +65,7 @@ int collision_max_ctas_per_sm(int N, int ctype, bool io_f64, int variant, int* c
 
 // Ragged launch: one persistent kernel over groups of cells with mixed N
 // (ragged_*.cu).  Groups are passed by value in the kernel parameters.
-constexpr int kMaxRaggedGroups = 32;
+constexpr int kMaxRaggedGroups = 256;
 struct RaggedItem {            // one group of cells evaluated with one plan
   const void* f;
   void* Q;

@@ -1,0 +1,237 @@
+"""Continuous-batching collision-evaluation service over the C ABI.
+
+Requests (cells x N^3, lambda, precision, a number of repeated evaluations)
+arrive over time.  Between GPU iterations the loop admits waiting requests in
+arrival order while they fit the HBM budget (f, Q and a share of the ragged
+workspace), keeps every admitted request's f resident on the device, and runs
+ONE ragged persistent launch per compute type over the cells of all active
+requests (coll_eval_ragged), followed by f <- f + dt Q (coll_advance).  A
+request leaves after its last evaluation; its memory returns to the budget and
+the next waiting requests join the following iteration.  Latency is measured
+from arrival to the completion of the request's last evaluation.
+
+Precision classes: "f32" runs the FP32 kernels; "mixed" runs float-pair
+(f32x2) transforms where the kernel supports the grid (N <= 32) and FP32 above.
+Each cell's arithmetic does not depend on what else is in the batch, so a
+request's result is the same alone and in the mix (tests/test_gpu_service.py).
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import json
+import math
+import time
+
+import numpy as np
+
+from . import coll, synth
+
+KIND = {"f32": "f32", "mixed": "f32x2"}
+
+
+def effective_precision(precision: str, N: int) -> str:
+    if precision == "mixed":
+        return "f32x2" if N <= 32 else "f32"
+    return precision
+
+
+@dataclasses.dataclass
+class Job:
+    rid: int
+    arrival_s: float
+    n_cells: int
+    N: int
+    lam: float
+    precision: str
+    n_evals: int = 10
+    dt: float = 1e-2
+    f_host: object = None           # optional numpy/torch host array; else generated on the device
+    seed: int = 0
+    # runtime
+    f: object = None
+    Q: object = None
+    done: int = 0
+    bytes: int = 0
+    t_admit: float = None
+    t_finish: float = None
+
+
+class Service:
+    def __init__(self, hbm_budget_bytes: float = 120e9, L: float = synth.DEFAULT_L, M: int = 48, Mtheta: int = 4,
+                 device: str = "cuda"):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.budget = int(hbm_budget_bytes)
+        self.L, self.M, self.Mtheta = L, M, Mtheta
+        self.plans = {}
+        self.stream = torch.cuda.Stream(device=self.device)
+        self.ws = None
+        self.in_use = 0
+        self.peak_in_use = 0
+        self.stats = collections.Counter()
+
+    # ---------------------------------------------------------------- plans
+    def plan(self, N: int, lam: float, prec: str):
+        key = (N, float(lam), prec)
+        if key not in self.plans:
+            Mr = 16 if lam == 1.0 else 8
+            self.plans[key] = coll.Plan(N, self.L, lam=lam, M=self.M, Mtheta=self.Mtheta, Mr=Mr, prec=prec,
+                                        max_cells=1, device=self.device)
+        return self.plans[key]
+
+    def warm_plans(self, Ns=(16, 32, 48, 64), lams=(0.0, 1.0), precisions=("f32", "mixed")):
+        for N in Ns:
+            for lam in lams:
+                for p in precisions:
+                    self.plan(N, lam, effective_precision(p, N))
+
+    # -------------------------------------------------------------- memory
+    def _job_bytes(self, j: Job) -> int:
+        prec = effective_precision(j.precision, j.N)
+        es = 8 if prec == "f32x2" else 4
+        return 2 * j.n_cells * j.N ** 3 * es
+
+    def _ensure_ws(self, nbytes: int):
+        if self.ws is None or self.ws.numel() < nbytes:
+            self.ws = self.torch.empty(int(nbytes * 1.25) + 256, dtype=self.torch.uint8, device=self.device)
+
+    def _admit(self, j: Job, now: float):
+        torch = self.torch
+        prec = effective_precision(j.precision, j.N)
+        dt = torch.float64 if prec == "f32x2" else torch.float32
+        with torch.cuda.stream(self.stream):
+            if j.f_host is not None:
+                src = torch.as_tensor(j.f_host)
+                j.f = src.to(self.device, dt, non_blocking=True)
+            else:
+                j.f = synth.bimodal_batch_device(j.n_cells, j.N, self.L, j.seed, dtype=dt, device=self.device)
+            j.Q = torch.empty_like(j.f)
+        j.bytes = self._job_bytes(j)
+        self.in_use += j.bytes
+        self.peak_in_use = max(self.peak_in_use, self.in_use)
+        j.t_admit = now
+
+    # ------------------------------------------------------------ one step
+    def _iterate(self, active):
+        """One evaluation of every active job: ragged launch per compute type, then f += dt Q."""
+        by_kind = collections.defaultdict(list)
+        for j in active:
+            by_kind[effective_precision(j.precision, j.N)].append(j)
+        for prec, jobs in by_kind.items():
+            for s in range(0, len(jobs), 256):
+                chunk = jobs[s:s + 256]
+                groups = [(self.plan(j.N, j.lam, prec).handle, j.f, j.Q) for j in chunk]
+                cells = [j.n_cells for j in chunk]
+                self._ensure_ws(coll.coll_ragged_workspace_size(groups, cells))
+                coll.coll_eval_ragged(groups, cells, self.ws, stream=self.stream)
+                self.stats["launches"] += 1
+        for j in active:
+            if j.done + 1 < j.n_evals:
+                coll.coll_advance(j.f, j.Q, j.dt, stream=self.stream)
+        self.stream.synchronize()
+        for j in active:
+            j.done += 1
+            self.stats["cell_evals"] += j.n_cells
+
+    # ----------------------------------------------------------------- run
+    def run(self, jobs, realtime: bool = True, max_wall_s: float = 600.0, keep_outputs: bool = False):
+        """Serve jobs (sorted by arrival).  Returns finished jobs and a stats dict.
+        realtime=False advances a simulated clock by the measured GPU time
+        (deterministic admission order); keep_outputs keeps each finished
+        job's final f and last Q on the device."""
+        pending = collections.deque(sorted(jobs, key=lambda j: j.arrival_s))
+        waiting = collections.deque()
+        active, finished = [], []
+        t0 = time.perf_counter()
+        clock = 0.0
+        max_q = 0
+        while pending or waiting or active:
+            now = time.perf_counter() - t0 if realtime else clock
+            if now > max_wall_s:
+                raise TimeoutError("service exceeded %.0f s" % max_wall_s)
+            while pending and pending[0].arrival_s <= now:
+                waiting.append(pending.popleft())
+            # admission: arrival order, skipping requests that do not fit yet
+            for j in list(waiting):
+                b = self._job_bytes(j)
+                if self.in_use + b <= self.budget:
+                    waiting.remove(j)
+                    self._admit(j, now)
+                    active.append(j)
+                elif b > self.budget:
+                    raise ValueError("request %d needs %d bytes > budget" % (j.rid, b))
+            max_q = max(max_q, len(waiting))
+            if not active:
+                if pending:
+                    nxt = pending[0].arrival_s
+                    if realtime:
+                        time.sleep(max(0.0, min(0.05, nxt - now)))
+                    else:
+                        clock = nxt
+                continue
+            t_it = time.perf_counter()
+            self._iterate(active)
+            if not realtime:
+                clock += time.perf_counter() - t_it
+            now = time.perf_counter() - t0 if realtime else clock
+            still = []
+            for j in active:
+                if j.done >= j.n_evals:
+                    j.t_finish = now
+                    self.in_use -= j.bytes
+                    if not keep_outputs:
+                        j.f = j.Q = None
+                    finished.append(j)
+                else:
+                    still.append(j)
+            active = still
+        wall = time.perf_counter() - t0 if realtime else clock
+        lat = np.array([j.t_finish - j.arrival_s for j in finished])
+        stats = {
+            "requests": len(finished),
+            "cell_evals": int(self.stats["cell_evals"]),
+            "wall_s": wall,
+            "cell_evals_per_s": self.stats["cell_evals"] / wall if wall > 0 else 0.0,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
+            "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
+            "peak_hbm_bytes": int(self.peak_in_use),
+            "hbm_budget_bytes": self.budget,
+            "max_queue_depth": int(max_q),
+            "ragged_launches": int(self.stats["launches"]),
+        }
+        return finished, stats
+
+    def close(self):
+        for p in self.plans.values():
+            p.close()
+        self.plans.clear()
+
+
+def stream_jobs(n_requests=2000, rate_per_s=200.0, seed=synth.BASE_SEED + 5, max_cells=2048,
+                Ns=(16, 32, 48, 64), n_evals=10):
+    """The serving workload: Poisson arrivals, log-uniform cell counts, mixed N,
+    lambda and precision (request_stream recipe), inputs drawn on the device."""
+    reqs = synth.request_stream(n_requests, rate_per_s, seed, Ns=Ns, max_cells=max_cells)
+    return [Job(r.rid, r.arrival_s, r.n_cells, r.N, r.lam, r.precision, n_evals=n_evals, seed=r.seed) for r in reqs]
+
+
+def main():
+    import argparse
+    ap = argparse.ArgumentParser(description="serve a Poisson stream of collision-evaluation requests")
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--budget-gb", type=float, default=120.0)
+    ap.add_argument("--max-cells", type=int, default=2048)
+    args = ap.parse_args()
+    svc = Service(hbm_budget_bytes=args.budget_gb * 1e9)
+    svc.warm_plans()
+    jobs = stream_jobs(args.requests, args.rate, max_cells=args.max_cells)
+    _, stats = svc.run(jobs)
+    print(json.dumps(stats))
+    svc.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -214,3 +214,24 @@ def request_stream(n_requests: int = 2000, rate_per_s: float = 200.0,
     prec = r.choice(np.array(precisions), size=n_requests)
     return [Request(i, float(t[i]), int(cells[i]), int(Nsel[i]), float(lam[i]), str(prec[i]),
                     seed * 7919 + i) for i in range(n_requests)]
+
+
+def bimodal_batch_device(n_cells: int, N: int, L: float, seed: int, dtype=None, device="cuda"):
+    """The bimodal recipe of ``bimodal_batch`` drawn on the device (torch), for
+    large serving workloads where host generation would dominate; parameters
+    from a seeded torch generator (not bitwise the numpy stream)."""
+    import torch
+    dtype = dtype or torch.float32
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    rho = torch.rand((n_cells, 2), generator=g, device=device, dtype=torch.float64) * 1.5 + 0.5
+    u = torch.rand((n_cells, 2, 3), generator=g, device=device, dtype=torch.float64) * 3.0 - 1.5
+    T = torch.rand((n_cells, 2), generator=g, device=device, dtype=torch.float64) * 1.5 + 0.5
+    x = -L + torch.arange(N, device=device, dtype=torch.float64) * (2.0 * L / N)
+    out = torch.zeros((n_cells, N, N, N), device=device, dtype=dtype)
+    for j in range(2):
+        e = [torch.exp(-(x[None, :] - u[:, j, d:d + 1]) ** 2 / (2.0 * T[:, j:j + 1])) for d in range(3)]
+        amp = rho[:, j] / (2.0 * math.pi * T[:, j]) ** 1.5
+        out += (amp[:, None, None, None] * e[0][:, :, None, None] * e[1][:, None, :, None]
+                * e[2][:, None, None, :]).to(dtype)
+    return out
