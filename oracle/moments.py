@@ -23,7 +23,7 @@ PSD is decided by the signs of the 7 principal minors of a symmetric 3x3 matrix.
 Bit-exactness.  The mask is an integer decided by floating point, so both the
 oracle and the GPU take the decision from the same numbers:
   * every sum over the grid is an exact integer: f is converted to fixed point
-    F = rint(f * 2^P) with a per-cell scale P = 61 - e, where e is the binary
+    F = trunc(f * 2^P) (toward zero) with a per-cell scale P = 61 - e, where e is the binary
     exponent with max|f| < 2^e (a max is order-independent too), and F is
     multiplied by integer grid monomials (v = dv k with k_d = j_d - N/2), so
     the sum is independent of order and resolves f to 2^-61 of its peak;
@@ -34,8 +34,9 @@ oracle and the GPU take the decision from the same numbers:
     project's own exponential (Cody-Waite reduction by ln 2 and a degree-13
     Horner Taylor polynomial), is rounded to fixed point E = rint(e 2^31), and
     M_fix = (A_fix E + 2^30) >> 31 with A_fix = rint(rho/(2 pi T)^{3/2} e0 e1 2^P2),
-    P2 = 61 - max(e, e_M) (e_M the exponent of the Maxwellian's peak), so
-    |F2 - M_fix| with F2 = rint(f 2^P2) is again an exact integer sum.
+    P2 = 30 - max(e, e_M) (e_M the exponent of the Maxwellian's peak), so
+    |F2 - M_fix| with F2 = trunc(f 2^P2) is again an exact integer sum; the L1
+    test resolves f and M to 2^-30 of the larger peak (32-bit integers).
 Eigenvalues of V_eps are reported (numpy eigvalsh), not bit-exact.
 """
 from __future__ import annotations
@@ -45,8 +46,9 @@ from decimal import Decimal, getcontext
 
 import numpy as np
 
-FIX_TOP = 61          # fixed-point values stay below 2^61 in magnitude
-E_BITS = 52
+FIX_TOP = 61          # fixed-point values of the moment sums stay below 2^61 in magnitude
+L1_TOP = 30           # fixed-point values of the L1 test stay below 2^30
+E_BITS = 31
 
 getcontext().prec = 60
 _LN2 = Decimal(2).ln()
@@ -85,8 +87,8 @@ def max_exponent(f: np.ndarray) -> int:
 
 
 def to_fixed(f: np.ndarray, P: int) -> np.ndarray:
-    """F = rint(f * 2^P) (round half to even) as exact Python ints (object array)."""
-    return np.rint(np.ldexp(np.asarray(f, dtype=np.float64), P)).astype(np.int64).astype(object)
+    """F = trunc(f * 2^P) (toward zero) as exact Python ints (object array)."""
+    return np.trunc(np.ldexp(np.asarray(f, dtype=np.float64), P)).astype(np.int64).astype(object)
 
 
 def _psd(S) -> bool:
@@ -203,7 +205,7 @@ def cell_moments(f: np.ndarray, L: float, eta0: float, delta0: float):
     # L1 distance to the Maxwellian with the same rho, u, T
     s = (2.0 * math.pi) * T
     CM = rho / (s * math.sqrt(s))
-    P2 = FIX_TOP - max(ef, math.frexp(CM)[1])
+    P2 = L1_TOP - max(ef, math.frexp(CM)[1])
     inv2T = 1.0 / (2.0 * T)
     e = []
     for d in range(3):

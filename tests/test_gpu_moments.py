@@ -74,6 +74,15 @@ def test_maxwellian_and_degenerate_cells():
     assert g[1, 0] == 0.0 and np.all(np.isnan(g[3]))
 
 
+@pytest.mark.parametrize("dtype,scales", [(np.float64, (-960, -995, -1030, -1060)), (np.float32, (-90, -110, -125))])
+def test_tiny_and_subnormal_cells(dtype, scales):
+    """Cells scaled toward and into the subnormal range (both conversion paths)."""
+    base = synth.bimodal_batch(1, 16, synth.DEFAULT_L, seed=77)[0]
+    f = np.stack([np.ldexp(base, e) for e in scales]).astype(dtype)
+    assert np.any((f != 0) & (np.abs(f) < np.finfo(dtype).tiny))
+    check(f, synth.DEFAULT_L)
+
+
 def test_threshold_cells_bit_exact():
     """eta0 placed 1e-9 (relative) either side of the largest |lambda - 1|."""
     N, L = 24, 10.0
