@@ -224,7 +224,9 @@ typedef struct {
  * Every grid sum is an exact fixed-point integer sum, so mom_out (except eig)
  * and mask_out are bitwise reproducible and independent of launch shape.
  * f, mom_out (n_cells records) and mask_out (n_cells bytes) are device
- * pointers.  n_cells = 0 is a no-op.
+ * pointers; N is even, 2 <= N <= 64.  Two kernels on the stream: the first
+ * streams f and leaves exact integer sums in mom_out (used as scratch), the
+ * second turns them into the records.  n_cells = 0 is a no-op.
  */
 coll_status moments_realizability(const void* f, int32_t io_dtype, int32_t N, double L,
                                   int64_t n_cells, double eta0, double delta0,

@@ -17,10 +17,11 @@
 // integer sum in 32-bit arithmetic.  Only the eigenvalues of V_eps (cyclic
 // Jacobi) are not bit-reproducible.
 //
-// Work per cell: one CTA.  Pass 0 takes max|f|; pass 1 walks rows (j0, j1)
-// and forms the five row sums sum_j2 F k2^c with 32x32->64-bit multiply-adds on
-// a 31-bit split of F, then folds them into the 14 global sums with the row's
-// k0, k1 weights; pass 2 (re-read from L2) accumulates |F2 - M_fix|.
+// Streaming work per cell: one CTA.  Pass 0 takes max|f|; pass 1 walks rows
+// (j0, j1) and forms the five row sums sum_j2 F k2^c with 32x32->64-bit
+// multiply-adds on a 31-bit split of F, then folds them into the 14 global sums
+// with the row's k0, k1 weights; pass 2 (re-read from L2) accumulates
+// |F2 - M_fix|.  The scalar algebra runs afterwards, one thread per cell.
 #include <cuda_runtime.h>
 
 #include "coll_internal.h"
@@ -221,288 +222,27 @@ __device__ __forceinline__ void block_sum(i128 (&v)[K], i128* red) {
   __syncthreads();
 }
 
-struct CellShared {
-  i128 red[(kMThreads / 32 + 1) * 14];
-  double e[3][64];
-  unsigned long long E2[64];
-  double bc[8];          // broadcast: CM, P2, valid flag ...
-  int ibc[4];
-  float fmax_f;
-  unsigned int anybad;
-  double fmax_d;
-};
 
-// Scalar algebra of one cell from its exact integer sums (thread 0 only):
-// moments, realizability and Euler-breakdown bits, and the Maxwellian
-// parameters of the L1 pass, in the oracle's order of operations.
-__device__ __noinline__ void scalar_part(const i128* acc, int P1, int ef, int N, double L, double eta0,
-                                         double* out, CellShared& sh) {
-  const double qnan = __longlong_as_double(0x7ff8000000000000ll);
-  double o[40];
-  for (int i = 0; i < 40; ++i) o[i] = qnan;
-  uint8_t mbits = 0;
-  const double h = ddiv(dmul(2.0, L), double(N));
-  const double vol = dmul(dmul(h, h), h);
-  const double D0 = i128_to_double(acc[0]);
-  const double rho = dmul(ldexp(D0, -P1), vol);
-  o[0] = rho;
-  sh.ibc[0] = 0;
-  if (!(D0 > 0.0)) {
-    mbits = 0x07;
-  } else {
-    const double inv0 = ddiv(1.0, D0);
-    double kap[3], u[3];
-    for (int d = 0; d < 3; ++d) {
-      kap[d] = dmul(i128_to_double(acc[1 + d]), inv0);
-      u[d] = dmul(kap[d], h);
-      o[1 + d] = u[d];
-    }
-    double m2[6];
-    const int pd[6] = {0, 1, 2, 0, 0, 1}, pe[6] = {0, 1, 2, 1, 2, 2};
-    for (int i = 0; i < 6; ++i) m2[i] = dmul(i128_to_double(acc[4 + i]), inv0);
-    double C[6];
-    for (int i = 0; i < 6; ++i) C[i] = dsub(m2[i], dmul(kap[pd[i]], kap[pe[i]]));
-    const double trC = dadd(dadd(C[0], C[1]), C[2]);
-    const double Tg = ddiv(trC, 3.0);
-    const double h2 = dmul(h, h);
-    const double T = dmul(Tg, h2);
-    o[4] = T;
-    if (!(Tg > 0.0)) {
-      mbits = 0x07;
-    } else {
-      double Theta[6], tau[6];
-      for (int i = 0; i < 6; ++i) Theta[i] = dmul(C[i], h2);
-      const double p = dmul(rho, T);
-      for (int i = 0; i < 6; ++i) tau[i] = i < 3 ? dsub(dmul(rho, Theta[i]), p) : dmul(rho, Theta[i]);
-      double E3[3];
-      for (int d = 0; d < 3; ++d) E3[d] = dmul(i128_to_double(acc[10 + d]), inv0);
-      const double kk = dadd(dadd(dmul(kap[0], kap[0]), dmul(kap[1], kap[1])), dmul(kap[2], kap[2]));
-      // symmetric access C(d, e)
-      auto Cs = [&](int d, int e) -> double {
-        if (d == e) return C[d];
-        const int lo = d < e ? d : e, hi = d < e ? e : d;
-        return lo == 0 ? (hi == 1 ? C[3] : C[4]) : C[5];
-      };
-      double m3[3], q[3];
-      const double rv = dmul(rho, vol);
-      for (int d = 0; d < 3; ++d) {
-        const double sC = dadd(dadd(dmul(kap[0], Cs(d, 0)), dmul(kap[1], Cs(d, 1))), dmul(kap[2], Cs(d, 2)));
-        m3[d] = dsub(dsub(dsub(E3[d], dmul(2.0, sC)), dmul(kap[d], trC)), dmul(kap[d], kk));
-        q[d] = dmul(0.5, dmul(rv, m3[d]));
-      }
-      const double E4 = dmul(i128_to_double(acc[13]), inv0);
-      const double kE3 = dadd(dadd(dmul(kap[0], E3[0]), dmul(kap[1], E3[1])), dmul(kap[2], E3[2]));
-      const double trm2 = dadd(dadd(m2[0], m2[1]), m2[2]);
-      const double km2k =
-          dadd(dadd(dadd(dmul(dmul(kap[0], kap[0]), m2[0]), dmul(dmul(kap[1], kap[1]), m2[1])),
-                    dmul(dmul(kap[2], kap[2]), m2[2])),
-               dmul(2.0, dadd(dadd(dmul(dmul(kap[0], kap[1]), m2[3]), dmul(dmul(kap[0], kap[2]), m2[4])),
-                              dmul(dmul(kap[1], kap[2]), m2[5]))));
-      const double m4 = dsub(dadd(dadd(dsub(E4, dmul(4.0, kE3)), dmul(dmul(2.0, kk), trm2)), dmul(4.0, km2k)),
-                             dmul(3.0, dmul(kk, kk)));
-      const double Cbar = dsub(ddiv(m4, dmul(10.0, dmul(Tg, Tg))), 0.5);
-      double Abar[6];
-      for (int i = 0; i < 6; ++i) Abar[i] = i < 3 ? dsub(ddiv(C[i], Tg), 1.0) : ddiv(C[i], Tg);
-      const double sq = dmul(Tg, __dsqrt_rn(Tg));
-      double Bbar[3];
-      for (int d = 0; d < 3; ++d) Bbar[d] = ddiv(dmul(0.5, m3[d]), sq);
-      const double c23 = 2.0 / 3.0;
-      double V[6];
-      for (int i = 0; i < 6; ++i) {
-        const double bb = dmul(Bbar[pd[i]], Bbar[pe[i]]);
-        V[i] = i < 3 ? dsub(dadd(1.0, Abar[i]), dmul(c23, bb)) : dsub(Abar[i], dmul(c23, bb));
-      }
-      bool realizable = false;
-      if (Cbar > 0.4) {
-        const double gam = ddiv(2.0, dmul(5.0, Cbar));
-        const double coef = ddiv(gam, dsub(1.0, gam));
-        double Vg[6];
-        for (int i = 0; i < 6; ++i) {
-          const double bb = dmul(Bbar[pd[i]], Bbar[pe[i]]);
-          Vg[i] = i < 3 ? dsub(dadd(1.0, Abar[i]), dmul(coef, bb)) : dsub(Abar[i], dmul(coef, bb));
-        }
-        realizable = psd3(Vg);
-      }
-      double up[6], dn[6];
-      for (int i = 0; i < 6; ++i) {
-        up[i] = i < 3 ? dsub(dadd(1.0, eta0), V[i]) : -V[i];
-        dn[i] = i < 3 ? dsub(V[i], dsub(1.0, eta0)) : V[i];
-      }
-      const bool near_euler = psd3(up) && psd3(dn);
-      mbits = (realizable ? 0 : 1) | (near_euler ? 0 : 2);
-      double ev[3];
-      eig3(V, ev);
-      // pack
-      for (int i = 0; i < 6; ++i) { o[5 + i] = Theta[i]; o[11 + i] = tau[i]; o[20 + i] = Abar[i]; o[30 + i] = V[i]; }
-      for (int d = 0; d < 3; ++d) { o[17 + d] = q[d]; o[26 + d] = Bbar[d]; o[36 + d] = ev[d]; }
-      o[29] = Cbar;
-      // Maxwellian parameters for pass 2
-      const double s = dmul(2.0 * 3.141592653589793, T);
-      const double CM = ddiv(rho, dmul(s, __dsqrt_rn(s)));
-      int eM;
-      frexp(CM, &eM);
-      const int P2 = kL1Top - (ef > eM ? ef : eM);
-      sh.bc[0] = CM;
-      sh.bc[1] = ddiv(1.0, dmul(2.0, T));
-      sh.bc[2] = h;
-      for (int d = 0; d < 3; ++d) sh.bc[3 + d] = u[d];
-      sh.ibc[0] = 1;
-      sh.ibc[1] = P2;
-    }
-  }
-  for (int i = 0; i < 40; ++i) out[i] = o[i];
-  sh.ibc[2] = mbits;
+// fold the five row sums R_c = sum_j2 F k2^c of row (k0, k1) into the 14
+// moment sums: sum F, sum F k_d, sum F k_d k_e, sum F k_d |k|^2, sum F |k|^4
+__device__ __forceinline__ void fold_row(i128 (&acc)[14], const i128 (&R)[5], long long k0, long long k1) {
+  const long long r2 = k0 * k0 + k1 * k1;
+  acc[0] += R[0];
+  acc[1] += R[0] * k0;
+  acc[2] += R[0] * k1;
+  acc[3] += R[1];
+  acc[4] += R[0] * (k0 * k0);
+  acc[5] += R[0] * (k1 * k1);
+  acc[6] += R[2];
+  acc[7] += R[0] * (k0 * k1);
+  acc[8] += R[1] * k0;
+  acc[9] += R[1] * k1;
+  acc[10] += R[0] * (k0 * r2) + R[2] * k0;
+  acc[11] += R[0] * (k1 * r2) + R[2] * k1;
+  acc[12] += R[1] * r2 + R[3];
+  acc[13] += R[0] * (r2 * r2) + R[2] * (2 * r2) + R[4];
 }
 
-template <typename Tio>
-__device__ void moments_cell(const Tio* __restrict__ f, int N, double L, double eta0, double delta0,
-                             coll_moments* mom, uint8_t* mask, CellShared& sh) {
-  const int tid = threadIdx.x;
-  const int n3 = N * N * N;
-  const int half = N / 2;
-
-  // ---- pass 0: max |f| and finiteness
-  double mx = 0.0;
-  bool bad = false;
-  for (int i = tid; i < n3; i += kMThreads) {
-    const Tio x = f[i];
-    bad |= !finite_val(x);
-    const double ax = double(absval(x));
-    mx = ax > mx ? ax : mx;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-  if (tid == 0) { sh.fmax_d = 0.0; sh.anybad = 0u; }
-  __syncthreads();
-  if ((tid & 31) == 0) {
-    atomicMax(reinterpret_cast<unsigned long long*>(&sh.fmax_d),
-              static_cast<unsigned long long>(__double_as_longlong(mx)));   // mx >= 0: bits order like values
-  }
-  if (bad) atomicOr(&sh.anybad, 1u);
-  __syncthreads();
-  const double fmaxv = sh.fmax_d;
-  const bool invalid = sh.anybad != 0u;
-  double* out = reinterpret_cast<double*>(mom);
-  const double qnan = __longlong_as_double(0x7ff8000000000000ll);
-  if (invalid || fmaxv == 0.0) {
-    if (tid < 40) out[tid] = (tid == 0 && !invalid) ? 0.0 : qnan;
-    if (tid == 0) *mask = invalid ? 0x87 : 0x07;
-    __syncthreads();
-    return;
-  }
-  int ef;
-  frexp(fmaxv, &ef);
-  const int P1 = kFixTop - ef;
-
-  // ---- pass 1: exact integer moment sums
-  i128 acc[14];
-#pragma unroll
-  for (int i = 0; i < 14; ++i) acc[i] = 0;
-  for (int row = tid; row < N * N; row += kMThreads) {
-    const int j0 = row / N, j1 = row % N;
-    const long long k0 = j0 - half, k1 = j1 - half;
-    long long rl[5] = {0, 0, 0, 0, 0}, rh[5] = {0, 0, 0, 0, 0};
-    const Tio* fr = f + size_t(row) * N;
-    for (int j2 = 0; j2 < N; ++j2) {
-      const long long F = fix_val(fr[j2], P1);
-      const int flo = int(F & 0x7fffffffll);
-      const int fhi = int(F >> 31);
-      const int k2 = j2 - half;
-      int kp = 1;
-#pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        rl[c] += static_cast<long long>(flo) * kp;
-        rh[c] += static_cast<long long>(fhi) * kp;
-        kp *= k2;
-      }
-    }
-    i128 R[5];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) R[c] = static_cast<i128>(rh[c]) * (static_cast<i128>(1) << 31) + static_cast<i128>(rl[c]);
-    const long long r2 = k0 * k0 + k1 * k1;
-    acc[0] += R[0];
-    acc[1] += R[0] * k0;
-    acc[2] += R[0] * k1;
-    acc[3] += R[1];
-    acc[4] += R[0] * (k0 * k0);
-    acc[5] += R[0] * (k1 * k1);
-    acc[6] += R[2];
-    acc[7] += R[0] * (k0 * k1);
-    acc[8] += R[1] * k0;
-    acc[9] += R[1] * k1;
-    acc[10] += R[0] * (k0 * r2) + R[2] * k0;
-    acc[11] += R[0] * (k1 * r2) + R[2] * k1;
-    acc[12] += R[1] * r2 + R[3];
-    acc[13] += R[0] * (r2 * r2) + R[2] * (2 * r2) + R[4];
-  }
-  block_sum<14>(acc, sh.red);
-
-  if (tid == 0) scalar_part(sh.red, P1, ef, N, L, eta0, out, sh);
-  __syncthreads();
-  if (sh.ibc[0] == 0) {
-    if (tid == 0) *mask = uint8_t(sh.ibc[2]);
-    __syncthreads();
-    return;
-  }
-  // ---- pass 2: L1 distance to the Maxwellian (exact integer sum)
-  const double CM = sh.bc[0], inv2T = sh.bc[1], h = sh.bc[2];
-  const int P2 = sh.ibc[1];
-  for (int i = tid; i < 3 * N; i += kMThreads) {
-    const int d = i / N, j = i % N;
-    const double x = dsub(dmul(h, double(j - half)), sh.bc[3 + d]);
-    sh.e[d][j] = own_exp(-dmul(dmul(x, x), inv2T));
-  }
-  __syncthreads();
-  if (tid < N) sh.E2[tid] = static_cast<unsigned long long>(__double2ll_rn(ldexp(sh.e[2][tid], kEBits)));
-  __syncthreads();
-  u128 l1acc = 0;
-  for (int row = tid; row < N * N; row += kMThreads) {
-    const int j0 = row / N, j1 = row % N;
-    const double A = dmul(dmul(CM, sh.e[0][j0]), sh.e[1][j1]);
-    const unsigned long long Af = static_cast<unsigned long long>(__double2ll_rn(ldexp(A, P2)));
-    const Tio* fr = f + size_t(row) * N;
-    for (int j2 = 0; j2 < N; ++j2) {
-      const long long F2 = fix_val(fr[j2], P2);
-      const unsigned long long E = sh.E2[j2];
-      unsigned long long lo = Af * E;
-      unsigned long long hi = __umul64hi(Af, E);
-      const unsigned long long add = 1ull << (kEBits - 1);
-      const unsigned long long lo2 = lo + add;
-      hi += (lo2 < lo) ? 1ull : 0ull;
-      const long long M = static_cast<long long>((hi << (64 - kEBits)) | (lo2 >> kEBits));
-      const long long dlt = F2 - M;
-      l1acc += static_cast<u128>(dlt < 0 ? -dlt : dlt);
-    }
-  }
-  i128 l1v[1] = {static_cast<i128>(l1acc)};
-  block_sum<1>(l1v, sh.red);
-  if (tid == 0) {
-    const double vol = dmul(dmul(h, h), h);
-    const double l1 = dmul(ldexp(i128_to_double(sh.red[0]), -P2), vol);
-    out[39] = l1;
-    uint8_t mb = uint8_t(sh.ibc[2]);
-    if (l1 > delta0) mb |= 4;
-    *mask = mb;
-  }
-  __syncthreads();
-}
-
-template <typename Tio>
-__global__ void __launch_bounds__(kMThreads, 4) moments_kernel(const Tio* __restrict__ f, int N, double L,
-                                                            long long n_cells, double eta0, double delta0,
-                                                            coll_moments* mom, uint8_t* mask) {
-  __shared__ CellShared sh;
-  const size_t n3 = size_t(N) * N * N;
-  for (long long c = blockIdx.x; c < n_cells; c += gridDim.x)
-    moments_cell<Tio>(f + size_t(c) * n3, N, L, eta0, delta0, mom + c, mask + c, sh);
-}
-
-
-// ------------------------------------------------------------------ fast path
-// Same cell computation with the grid size N known at compile time: rows are
-// read with 16-byte vector loads, every k2 power is an immediate constant and
-// the row loops unroll, so the passes stream at memory speed instead of
-// waiting on one load at a time.
 template <typename Tio> struct Bits;
 // trunc(t * 2^(-k)) for t < 2^62 and k >= 1 (t >> 63 is already 0)
 __device__ __forceinline__ unsigned long long rshift_trunc(unsigned long long t, int k) {
@@ -592,9 +332,321 @@ __device__ __forceinline__ void load8(const Tio* p, typename Bits<Tio>::U* b) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Two launches per batch.
+//
+//   K1 (one CTA per cell, persistent over cells): pass 0 (max |f|, finiteness),
+//      pass 1 (the 14 exact moment sums), the Maxwellian parameters rho, u, T
+//      (a short serial section), pass 2 (the exact L1 sum).  It leaves the
+//      integer results in the cell's output record, used as scratch.
+//   K2 (one thread per cell): the scalar algebra of the record (tensors,
+//      realizability and Euler-breakdown tests, eigenvalues) from those
+//      integers, overwriting the scratch with the final record and mask.
+//
+// FP64 runs at a small fraction of the integer rate on this GPU, so the long
+// dependent chain of correctly rounded divisions and square roots per cell is
+// taken off the streaming CTAs and run for all cells side by side.
+// ---------------------------------------------------------------------------
+
+// scratch words in the 40-double record written by K1 and read by K2
+enum : int {
+  kWSums = 0,      // 14 sums as (low, high) 64-bit words: words 0..27
+  kWState = 28,    // 0: finite, non-zero cell; 1: non-finite value; 2: all zero
+  kWP1 = 29,       // scale of the moment sums
+  kWL1Lo = 30,     // exact L1 sum (unsigned 128-bit), valid when kWHasL1 = 1
+  kWL1Hi = 31,
+  kWP2 = 32,       // scale of the L1 sum
+  kWHasL1 = 33,
+};
+
+struct CellShared {
+  i128 red[(kMThreads / 32 + 1) * 14];
+  double e[3][64];
+  unsigned long long E2[64];
+  double dsum[7];
+  double bc[8];          // broadcast: CM, 1/(2T), h, u[3]
+  int ibc[4];            // broadcast: Maxwellian valid, P2
+  unsigned int anybad;
+  double fmax_d;
+};
+
+// rho, u, T and the quantities they are built from, from the first 7 sums
+// rounded to double (D[0] = sum F, D[1..3] = sum F k_d, D[4..6] = sum F k_d^2).
+// The same sequence of operations serves K1 (Maxwellian of the L1 test) and K2
+// (the record), so both see bitwise identical values.
+struct Basic {
+  double h, vol, h2, rho, inv0, kap[3], u[3], m2d[3], C[3], trC, Tg, T;
+};
+__device__ __forceinline__ void basic_moments(const double* D, int P1, int N, double L, Basic& b) {
+  b.h = ddiv(dmul(2.0, L), double(N));
+  b.vol = dmul(dmul(b.h, b.h), b.h);
+  b.rho = dmul(ldexp(D[0], -P1), b.vol);
+  b.h2 = dmul(b.h, b.h);
+  if (!(D[0] > 0.0)) return;
+  b.inv0 = ddiv(1.0, D[0]);
+  for (int d = 0; d < 3; ++d) {
+    b.kap[d] = dmul(D[1 + d], b.inv0);
+    b.u[d] = dmul(b.kap[d], b.h);
+  }
+  for (int d = 0; d < 3; ++d) {
+    b.m2d[d] = dmul(D[4 + d], b.inv0);
+    b.C[d] = dsub(b.m2d[d], dmul(b.kap[d], b.kap[d]));
+  }
+  b.trC = dadd(dadd(b.C[0], b.C[1]), b.C[2]);
+  b.Tg = ddiv(b.trC, 3.0);
+  b.T = dmul(b.Tg, b.h2);
+}
+
+// Scalar algebra of one cell from its exact integer sums: the record o[0..38]
+// and the realizability / Euler-breakdown bits, in the oracle's order of
+// operations.  Returns false (mask 0x07) for a cell without positive density
+// or temperature.
+__device__ bool scalar_part(const i128* acc, int P1, int N, double L, double eta0, double* o, uint8_t& mbits) {
+  double D[7];
+  for (int i = 0; i < 7; ++i) D[i] = i128_to_double(acc[i]);
+  Basic b;
+  basic_moments(D, P1, N, L, b);
+  o[0] = b.rho;
+  if (!(D[0] > 0.0)) { mbits = 0x07; return false; }
+  for (int d = 0; d < 3; ++d) o[1 + d] = b.u[d];
+  o[4] = b.T;
+  if (!(b.Tg > 0.0)) { mbits = 0x07; return false; }
+  const double* kap = b.kap;
+  const double inv0 = b.inv0, Tg = b.Tg, h2 = b.h2, rho = b.rho, trC = b.trC;
+  double m2[6], C[6];
+  for (int d = 0; d < 3; ++d) { m2[d] = b.m2d[d]; C[d] = b.C[d]; }
+  const int pd[6] = {0, 1, 2, 0, 0, 1}, pe[6] = {0, 1, 2, 1, 2, 2};
+  for (int i = 3; i < 6; ++i) {
+    m2[i] = dmul(i128_to_double(acc[4 + i]), inv0);
+    C[i] = dsub(m2[i], dmul(kap[pd[i]], kap[pe[i]]));
+  }
+  double Theta[6], tau[6];
+  for (int i = 0; i < 6; ++i) Theta[i] = dmul(C[i], h2);
+  const double p = dmul(rho, b.T);
+  for (int i = 0; i < 6; ++i) tau[i] = i < 3 ? dsub(dmul(rho, Theta[i]), p) : dmul(rho, Theta[i]);
+  double E3[3];
+  for (int d = 0; d < 3; ++d) E3[d] = dmul(i128_to_double(acc[10 + d]), inv0);
+  const double kk = dadd(dadd(dmul(kap[0], kap[0]), dmul(kap[1], kap[1])), dmul(kap[2], kap[2]));
+  auto Cs = [&](int d, int e) -> double {       // symmetric access C(d, e)
+    if (d == e) return C[d];
+    const int lo = d < e ? d : e, hi = d < e ? e : d;
+    return lo == 0 ? (hi == 1 ? C[3] : C[4]) : C[5];
+  };
+  double m3[3], q[3];
+  const double rv = dmul(rho, b.vol);
+  for (int d = 0; d < 3; ++d) {
+    const double sC = dadd(dadd(dmul(kap[0], Cs(d, 0)), dmul(kap[1], Cs(d, 1))), dmul(kap[2], Cs(d, 2)));
+    m3[d] = dsub(dsub(dsub(E3[d], dmul(2.0, sC)), dmul(kap[d], trC)), dmul(kap[d], kk));
+    q[d] = dmul(0.5, dmul(rv, m3[d]));
+  }
+  const double E4 = dmul(i128_to_double(acc[13]), inv0);
+  const double kE3 = dadd(dadd(dmul(kap[0], E3[0]), dmul(kap[1], E3[1])), dmul(kap[2], E3[2]));
+  const double trm2 = dadd(dadd(m2[0], m2[1]), m2[2]);
+  const double km2k =
+      dadd(dadd(dadd(dmul(dmul(kap[0], kap[0]), m2[0]), dmul(dmul(kap[1], kap[1]), m2[1])),
+                dmul(dmul(kap[2], kap[2]), m2[2])),
+           dmul(2.0, dadd(dadd(dmul(dmul(kap[0], kap[1]), m2[3]), dmul(dmul(kap[0], kap[2]), m2[4])),
+                          dmul(dmul(kap[1], kap[2]), m2[5]))));
+  const double m4 = dsub(dadd(dadd(dsub(E4, dmul(4.0, kE3)), dmul(dmul(2.0, kk), trm2)), dmul(4.0, km2k)),
+                         dmul(3.0, dmul(kk, kk)));
+  const double Cbar = dsub(ddiv(m4, dmul(10.0, dmul(Tg, Tg))), 0.5);
+  double Abar[6];
+  for (int i = 0; i < 6; ++i) Abar[i] = i < 3 ? dsub(ddiv(C[i], Tg), 1.0) : ddiv(C[i], Tg);
+  const double sq = dmul(Tg, __dsqrt_rn(Tg));
+  double Bbar[3];
+  for (int d = 0; d < 3; ++d) Bbar[d] = ddiv(dmul(0.5, m3[d]), sq);
+  const double c23 = 2.0 / 3.0;
+  double V[6];
+  for (int i = 0; i < 6; ++i) {
+    const double bb = dmul(Bbar[pd[i]], Bbar[pe[i]]);
+    V[i] = i < 3 ? dsub(dadd(1.0, Abar[i]), dmul(c23, bb)) : dsub(Abar[i], dmul(c23, bb));
+  }
+  bool realizable = false;
+  if (Cbar > 0.4) {
+    const double gam = ddiv(2.0, dmul(5.0, Cbar));
+    const double coef = ddiv(gam, dsub(1.0, gam));
+    double Vg[6];
+    for (int i = 0; i < 6; ++i) {
+      const double bb = dmul(Bbar[pd[i]], Bbar[pe[i]]);
+      Vg[i] = i < 3 ? dsub(dadd(1.0, Abar[i]), dmul(coef, bb)) : dsub(Abar[i], dmul(coef, bb));
+    }
+    realizable = psd3(Vg);
+  }
+  double up[6], dn[6];
+  for (int i = 0; i < 6; ++i) {
+    up[i] = i < 3 ? dsub(dadd(1.0, eta0), V[i]) : -V[i];
+    dn[i] = i < 3 ? dsub(V[i], dsub(1.0, eta0)) : V[i];
+  }
+  const bool near_euler = psd3(up) && psd3(dn);
+  mbits = (realizable ? 0 : 1) | (near_euler ? 0 : 2);
+  double ev[3];
+  eig3(V, ev);
+  for (int i = 0; i < 6; ++i) { o[5 + i] = Theta[i]; o[11 + i] = tau[i]; o[20 + i] = Abar[i]; o[30 + i] = V[i]; }
+  for (int d = 0; d < 3; ++d) { o[17 + d] = q[d]; o[26 + d] = Bbar[d]; o[36 + d] = ev[d]; }
+  o[29] = Cbar;
+  return true;
+}
+
+// ---- K1 pieces shared by the runtime-N and compile-time-N cell functions
+
+// Pass-0 epilogue: block max / finiteness; writes the scratch state of an
+// invalid or all-zero cell and returns false for it.
+__device__ __forceinline__ bool cell_state(unsigned long long mx_bits, bool bad, unsigned long long* w, CellShared& sh,
+                                           double* fmaxv) {
+  const int tid = threadIdx.x;
+  if (tid == 0) { sh.fmax_d = 0.0; sh.anybad = 0u; }
+  __syncthreads();
+  if ((tid & 31) == 0) atomicMax(reinterpret_cast<unsigned long long*>(&sh.fmax_d), mx_bits);
+  if (bad) atomicOr(&sh.anybad, 1u);
+  __syncthreads();
+  *fmaxv = sh.fmax_d;
+  const bool invalid = sh.anybad != 0u;
+  if (invalid || *fmaxv == 0.0) {
+    if (tid == 0) w[kWState] = invalid ? 1ull : 2ull;
+    __syncthreads();
+    return false;
+  }
+  return true;
+}
+
+// After pass 1: store the sums and P1, then the Maxwellian of the L1 test
+// (serial part, thread 0) into sh.bc / sh.ibc.  Returns whether pass 2 runs.
+__device__ __forceinline__ bool after_sums(i128 (&acc)[14], int P1, int ef, int N, double L, unsigned long long* w,
+                                           CellShared& sh) {
+  const int tid = threadIdx.x;
+  block_sum<14>(acc, sh.red);
+  if (tid < 28) {
+    const u128 v = static_cast<u128>(sh.red[tid >> 1]);
+    w[kWSums + tid] = (tid & 1) ? static_cast<unsigned long long>(v >> 64) : static_cast<unsigned long long>(v);
+  } else if (tid < 35) {
+    sh.dsum[tid - 28] = i128_to_double(sh.red[tid - 28]);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    w[kWState] = 0;
+    w[kWP1] = static_cast<unsigned long long>(static_cast<long long>(P1));
+    Basic b;
+    basic_moments(sh.dsum, P1, N, L, b);
+    const bool ok = sh.dsum[0] > 0.0 && b.Tg > 0.0;
+    sh.ibc[0] = ok;
+    w[kWHasL1] = ok;
+    if (ok) {
+      const double s = dmul(2.0 * 3.141592653589793, b.T);
+      const double CM = ddiv(b.rho, dmul(s, __dsqrt_rn(s)));
+      int eM;
+      frexp(CM, &eM);
+      const int P2 = kL1Top - (ef > eM ? ef : eM);
+      sh.bc[0] = CM;
+      sh.bc[1] = ddiv(1.0, dmul(2.0, b.T));
+      sh.bc[2] = b.h;
+      for (int d = 0; d < 3; ++d) sh.bc[3 + d] = b.u[d];
+      sh.ibc[1] = P2;
+      w[kWP2] = static_cast<unsigned long long>(static_cast<long long>(P2));
+    }
+  }
+  __syncthreads();
+  return sh.ibc[0] != 0;
+}
+
+// 1D factors of the separable Maxwellian: e_d[j] = exp(-(h (j - N/2) - u_d)^2 / (2T)),
+// and the k2 factor in 31-bit fixed point.
+__device__ __forceinline__ void maxwell_factors(int N, CellShared& sh) {
+  const int tid = threadIdx.x, half = N / 2;
+  const double inv2T = sh.bc[1], h = sh.bc[2];
+  for (int i = tid; i < 3 * N; i += kMThreads) {
+    const int d = i / N, j = i % N;
+    const double x = dsub(dmul(h, double(j - half)), sh.bc[3 + d]);
+    sh.e[d][j] = own_exp(-dmul(dmul(x, x), inv2T));
+  }
+  __syncthreads();
+  if (tid < N) sh.E2[tid] = static_cast<unsigned long long>(__double2ll_rn(ldexp(sh.e[2][tid], kEBits)));
+  __syncthreads();
+}
+
+__device__ __forceinline__ void store_l1(u128 l1acc, unsigned long long* w, CellShared& sh) {
+  i128 l1v[1] = {static_cast<i128>(l1acc)};
+  block_sum<1>(l1v, sh.red);
+  if (threadIdx.x == 0) {
+    const u128 v = static_cast<u128>(sh.red[0]);
+    w[kWL1Lo] = static_cast<unsigned long long>(v);
+    w[kWL1Hi] = static_cast<unsigned long long>(v >> 64);
+  }
+  __syncthreads();
+}
+
+// ---- K1, runtime N (any even N <= 64, any alignment)
+template <typename Tio>
+__device__ void sums_cell(const Tio* __restrict__ f, int N, double L, unsigned long long* w, CellShared& sh) {
+  const int tid = threadIdx.x;
+  const int n3 = N * N * N;
+  const int half = N / 2;
+
+  double mx = 0.0;
+  bool bad = false;
+  for (int i = tid; i < n3; i += kMThreads) {
+    const Tio x = f[i];
+    bad |= !finite_val(x);
+    const double ax = double(absval(x));
+    mx = ax > mx ? ax : mx;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  double fmaxv;      // mx >= 0: the bit patterns order like the values
+  if (!cell_state(static_cast<unsigned long long>(__double_as_longlong(mx)), bad, w, sh, &fmaxv)) return;
+  int ef;
+  frexp(fmaxv, &ef);
+  const int P1 = kFixTop - ef;
+
+  i128 acc[14];
+#pragma unroll
+  for (int i = 0; i < 14; ++i) acc[i] = 0;
+  for (int row = tid; row < N * N; row += kMThreads) {
+    const int j0 = row / N, j1 = row % N;
+    const long long k0 = j0 - half, k1 = j1 - half;
+    long long rl[5] = {0, 0, 0, 0, 0}, rh[5] = {0, 0, 0, 0, 0};
+    const Tio* fr = f + size_t(row) * N;
+    for (int j2 = 0; j2 < N; ++j2) {
+      const long long F = fix_val(fr[j2], P1);
+      const int flo = int(F & 0x7fffffffll);
+      const int fhi = int(F >> 31);
+      const int k2 = j2 - half;
+      int kp = 1;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        rl[c] += static_cast<long long>(flo) * kp;
+        rh[c] += static_cast<long long>(fhi) * kp;
+        kp *= k2;
+      }
+    }
+    i128 R[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) R[c] = static_cast<i128>(rh[c]) * (static_cast<i128>(1) << 31) + static_cast<i128>(rl[c]);
+    fold_row(acc, R, k0, k1);
+  }
+  if (!after_sums(acc, P1, ef, N, L, w, sh)) return;
+
+  maxwell_factors(N, sh);
+  const double CM = sh.bc[0];
+  const int P2 = sh.ibc[1];
+  u128 l1acc = 0;
+  for (int row = tid; row < N * N; row += kMThreads) {
+    const int j0 = row / N, j1 = row % N;
+    const double A = dmul(dmul(CM, sh.e[0][j0]), sh.e[1][j1]);
+    const unsigned long long Af = static_cast<unsigned long long>(__double2ll_rn(ldexp(A, P2)));   // < 2^30
+    const Tio* fr = f + size_t(row) * N;
+    for (int j2 = 0; j2 < N; ++j2) {
+      const long long F2 = fix_val(fr[j2], P2);
+      const long long M = static_cast<long long>((Af * sh.E2[j2] + (1ull << (kEBits - 1))) >> kEBits);
+      const long long dlt = F2 - M;
+      l1acc += static_cast<u128>(dlt < 0 ? -dlt : dlt);
+    }
+  }
+  store_l1(l1acc, w, sh);
+}
+
+// ---- K1, compile-time N over bit patterns (16-byte aligned f)
 template <int N, typename Tio>
-__device__ void moments_cell_fast(const Tio* __restrict__ f, double L, double eta0, double delta0,
-                                  coll_moments* mom, uint8_t* mask, CellShared& sh) {
+__device__ void sums_cell_fast(const Tio* __restrict__ f, double L, unsigned long long* w, CellShared& sh) {
   using B = Bits<Tio>;
   using U = typename B::U;
   constexpr int half = N / 2;
@@ -602,7 +654,7 @@ __device__ void moments_cell_fast(const Tio* __restrict__ f, double L, double et
   constexpr int VEC = 16 / int(sizeof(Tio));
   const int tid = threadIdx.x;
 
-  // ---- pass 0: max |f| (integer max of the magnitude bits) and finiteness
+  // pass 0: max |f| as an integer max of the magnitude bits, finiteness
   U mx = 0;
   bool bad = false;
   const uint4* f4 = reinterpret_cast<const uint4*>(f);
@@ -623,33 +675,21 @@ __device__ void moments_cell_fast(const Tio* __restrict__ f, double L, double et
     }
   }
   mx = B::shfl_max(mx);
-  if (tid == 0) { sh.fmax_d = 0.0; sh.anybad = 0u; }
-  __syncthreads();
-  if ((tid & 31) == 0) atomicMax(reinterpret_cast<unsigned long long*>(&sh.fmax_d), (unsigned long long)mx);
-  if (bad) atomicOr(&sh.anybad, 1u);
-  __syncthreads();
-  const double fmaxv = B::value((U)(*reinterpret_cast<unsigned long long*>(&sh.fmax_d)));
-  const bool invalid = sh.anybad != 0u;
-  double* out = reinterpret_cast<double*>(mom);
-  const double qnan = __longlong_as_double(0x7ff8000000000000ll);
-  if (invalid || fmaxv == 0.0) {
-    if (tid < 40) out[tid] = (tid == 0 && !invalid) ? 0.0 : qnan;
-    if (tid == 0) *mask = invalid ? 0x87 : 0x07;
-    __syncthreads();
-    return;
-  }
+  double fmaxv;
+  const unsigned long long mxd = static_cast<unsigned long long>(__double_as_longlong(B::value(mx)));
+  if (!cell_state(mxd, bad, w, sh, &fmaxv)) return;
   int ef;
   frexp(fmaxv, &ef);
   // The bit-pattern conversions below assume a cell maximum well above the
   // subnormal range (shift counts stay non-negative, subnormal entries of the
   // L1 pass truncate to 0); a cell of tinier values takes the general path.
   if (ef < (sizeof(Tio) == 8 ? -990 : -100)) {
-    moments_cell<Tio>(f, N, L, eta0, delta0, mom, mask, sh);
+    sums_cell<Tio>(f, N, L, w, sh);
     return;
   }
   const int P1 = kFixTop - ef;
 
-  // ---- pass 1: exact integer moment sums, rows of N with immediate k2 powers
+  // pass 1: rows of N with immediate k2 powers
   i128 acc[14];
 #pragma unroll
   for (int i = 0; i < 14; ++i) acc[i] = 0;
@@ -678,41 +718,14 @@ __device__ void moments_cell_fast(const Tio* __restrict__ f, double L, double et
     i128 R[5];
 #pragma unroll
     for (int c = 0; c < 5; ++c) R[c] = static_cast<i128>(rh[c]) * (static_cast<i128>(1) << 31) + static_cast<i128>(rl[c]);
-    const long long r2 = k0 * k0 + k1 * k1;
-    acc[0] += R[0];
-    acc[1] += R[0] * k0;
-    acc[2] += R[0] * k1;
-    acc[3] += R[1];
-    acc[4] += R[0] * (k0 * k0);
-    acc[5] += R[0] * (k1 * k1);
-    acc[6] += R[2];
-    acc[7] += R[0] * (k0 * k1);
-    acc[8] += R[1] * k0;
-    acc[9] += R[1] * k1;
-    acc[10] += R[0] * (k0 * r2) + R[2] * k0;
-    acc[11] += R[0] * (k1 * r2) + R[2] * k1;
-    acc[12] += R[1] * r2 + R[3];
-    acc[13] += R[0] * (r2 * r2) + R[2] * (2 * r2) + R[4];
+    fold_row(acc, R, k0, k1);
   }
-  block_sum<14>(acc, sh.red);
-  if (tid == 0) scalar_part(sh.red, P1, ef, N, L, eta0, out, sh);
-  __syncthreads();
-  if (sh.ibc[0] == 0) {
-    if (tid == 0) *mask = uint8_t(sh.ibc[2]);
-    __syncthreads();
-    return;
-  }
-  // ---- pass 2: L1 distance to the Maxwellian (exact integer sum)
-  const double CM = sh.bc[0], inv2T = sh.bc[1], h = sh.bc[2];
+  if (!after_sums(acc, P1, ef, N, L, w, sh)) return;
+
+  // pass 2: L1 distance to the Maxwellian in 32-bit fixed point
+  maxwell_factors(N, sh);
+  const double CM = sh.bc[0];
   const int P2 = sh.ibc[1];
-  for (int i = tid; i < 3 * N; i += kMThreads) {
-    const int d = i / N, j = i % N;
-    const double x = dsub(dmul(h, double(j - half)), sh.bc[3 + d]);
-    sh.e[d][j] = own_exp(-dmul(dmul(x, x), inv2T));
-  }
-  __syncthreads();
-  if (tid < N) sh.E2[tid] = static_cast<unsigned long long>(__double2ll_rn(ldexp(sh.e[2][tid], kEBits)));
-  __syncthreads();
   unsigned long long l1acc = 0;                      // < 2^18 values of < 2^31 each
   for (int row = tid; row < N * N; row += kMThreads) {
     const int j0 = row / N, j1 = row % N;
@@ -733,84 +746,109 @@ __device__ void moments_cell_fast(const Tio* __restrict__ f, double L, double et
       }
     }
   }
-  i128 l1v[1] = {static_cast<i128>(l1acc)};
-  block_sum<1>(l1v, sh.red);
-  if (tid == 0) {
-    const double vol = dmul(dmul(h, h), h);
-    const double l1 = dmul(ldexp(i128_to_double(sh.red[0]), -P2), vol);
-    out[39] = l1;
-    uint8_t mb = uint8_t(sh.ibc[2]);
-    if (l1 > delta0) mb |= 4;
-    *mask = mb;
-  }
-  __syncthreads();
+  store_l1(l1acc, w, sh);
+}
+
+template <typename Tio>
+__global__ void __launch_bounds__(kMThreads, 4) sums_kernel(const Tio* __restrict__ f, int N, double L,
+                                                         long long n_cells, coll_moments* mom) {
+  __shared__ CellShared sh;
+  const size_t n3 = size_t(N) * N * N;
+  for (long long c = blockIdx.x; c < n_cells; c += gridDim.x)
+    sums_cell<Tio>(f + size_t(c) * n3, N, L, reinterpret_cast<unsigned long long*>(mom + c), sh);
 }
 
 template <int N, typename Tio>
-__global__ void __launch_bounds__(kMThreads, 4) moments_kernel_fast(const Tio* __restrict__ f, double L,
-                                                                 long long n_cells, double eta0, double delta0,
-                                                                 coll_moments* mom, uint8_t* mask) {
+__global__ void __launch_bounds__(kMThreads, 4) sums_kernel_fast(const Tio* __restrict__ f, double L,
+                                                              long long n_cells, coll_moments* mom) {
   __shared__ CellShared sh;
   constexpr size_t n3 = size_t(N) * N * N;
   for (long long c = blockIdx.x; c < n_cells; c += gridDim.x)
-    moments_cell_fast<N, Tio>(f + size_t(c) * n3, L, eta0, delta0, mom + c, mask + c, sh);
+    sums_cell_fast<N, Tio>(f + size_t(c) * n3, L, reinterpret_cast<unsigned long long*>(mom + c), sh);
 }
 
-template <int N, typename Tio>
-int launch_fast(const Tio* f, double L, long long n_cells, double eta0, double delta0, coll_moments* mom,
-                uint8_t* mask, cudaStream_t st) {
+// ---- K2: one thread per cell
+constexpr int kFinishThreads = 32;
+
+__global__ void __launch_bounds__(kFinishThreads) finish_kernel(int N, double L, long long n_cells, double eta0,
+                                                                double delta0, coll_moments* mom, uint8_t* mask) {
+  const long long c = static_cast<long long>(blockIdx.x) * kFinishThreads + threadIdx.x;
+  if (c >= n_cells) return;
+  unsigned long long* w = reinterpret_cast<unsigned long long*>(mom + c);
+  double* out = reinterpret_cast<double*>(mom + c);
+  const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+  double o[40];
+  for (int i = 0; i < 40; ++i) o[i] = qnan;
+  uint8_t mbits;
+  const unsigned long long state = w[kWState];
+  if (state != 0) {
+    if (state == 2) o[0] = 0.0;
+    mbits = state == 1 ? 0x87 : 0x07;
+  } else {
+    i128 acc[14];
+    for (int i = 0; i < 14; ++i)
+      acc[i] = static_cast<i128>((static_cast<u128>(w[kWSums + 2 * i + 1]) << 64) | static_cast<u128>(w[kWSums + 2 * i]));
+    const int P1 = static_cast<int>(static_cast<long long>(w[kWP1]));
+    const bool has_l1 = w[kWHasL1] != 0;
+    const u128 l1s = (static_cast<u128>(w[kWL1Hi]) << 64) | static_cast<u128>(w[kWL1Lo]);
+    const int P2 = static_cast<int>(static_cast<long long>(w[kWP2]));
+    if (scalar_part(acc, P1, N, L, eta0, o, mbits) && has_l1) {
+      const double h = ddiv(dmul(2.0, L), double(N));
+      const double vol = dmul(dmul(h, h), h);
+      const double l1 = dmul(ldexp(i128_to_double(static_cast<i128>(l1s)), -P2), vol);
+      o[39] = l1;
+      if (l1 > delta0) mbits |= 4;
+    }
+  }
+  for (int i = 0; i < 40; ++i) out[i] = o[i];
+  mask[c] = mbits;
+}
+
+int grid_for(const void* kernel, long long n_cells) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, moments_kernel_fast<N, Tio>, kMThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kMThreads, 0);
   if (per < 1) per = 1;
   long long grid = static_cast<long long>(sms) * per;
-  if (grid > n_cells) grid = n_cells;
-  moments_kernel_fast<N, Tio><<<int(grid), kMThreads, 0, st>>>(f, L, n_cells, eta0, delta0, mom, mask);
+  return int(grid > n_cells ? n_cells : grid);
+}
+
+template <int N, typename Tio>
+int launch_fast(const Tio* f, double L, long long n_cells, coll_moments* mom, cudaStream_t st) {
+  const int grid = grid_for(reinterpret_cast<const void*>(sums_kernel_fast<N, Tio>), n_cells);
+  sums_kernel_fast<N, Tio><<<grid, kMThreads, 0, st>>>(f, L, n_cells, mom);
   return int(cudaGetLastError());
 }
 
 template <typename Tio>
-int dispatch_fast(int N, const Tio* f, double L, long long n_cells, double eta0, double delta0, coll_moments* mom,
-                  uint8_t* mask, cudaStream_t st) {
-  switch (N) {
-    case 16: return launch_fast<16, Tio>(f, L, n_cells, eta0, delta0, mom, mask, st);
-    case 24: return launch_fast<24, Tio>(f, L, n_cells, eta0, delta0, mom, mask, st);
-    case 32: return launch_fast<32, Tio>(f, L, n_cells, eta0, delta0, mom, mask, st);
-    case 48: return launch_fast<48, Tio>(f, L, n_cells, eta0, delta0, mom, mask, st);
-    case 64: return launch_fast<64, Tio>(f, L, n_cells, eta0, delta0, mom, mask, st);
+int launch_sums(const Tio* f, int N, double L, long long n_cells, coll_moments* mom, cudaStream_t st) {
+  if ((reinterpret_cast<uintptr_t>(f) & 15u) == 0) {
+    switch (N) {
+      case 16: return launch_fast<16, Tio>(f, L, n_cells, mom, st);
+      case 24: return launch_fast<24, Tio>(f, L, n_cells, mom, st);
+      case 32: return launch_fast<32, Tio>(f, L, n_cells, mom, st);
+      case 48: return launch_fast<48, Tio>(f, L, n_cells, mom, st);
+      case 64: return launch_fast<64, Tio>(f, L, n_cells, mom, st);
+      default: break;
+    }
   }
-  return -1;
+  const int grid = grid_for(reinterpret_cast<const void*>(sums_kernel<Tio>), n_cells);
+  sums_kernel<Tio><<<grid, kMThreads, 0, st>>>(f, N, L, n_cells, mom);
+  return int(cudaGetLastError());
 }
 
 }  // namespace
 
 int launch_moments(const void* f, int io_f64, int N, double L, long long n_cells, double eta0, double delta0,
                    coll_moments* mom, uint8_t* mask, void* stream) {
-  count_launches(1);
+  count_launches(2);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // the compile-time-N kernel for the supported grids (16-byte aligned input)
-  if ((reinterpret_cast<uintptr_t>(f) & 15u) == 0) {
-    const int r = io_f64 ? dispatch_fast<double>(N, static_cast<const double*>(f), L, n_cells, eta0, delta0, mom, mask, st)
-                         : dispatch_fast<float>(N, static_cast<const float*>(f), L, n_cells, eta0, delta0, mom, mask, st);
-    if (r != -1) return r;
-  }
-  int dev = 0, sms = 0, per = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (io_f64)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, moments_kernel<double>, kMThreads, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, moments_kernel<float>, kMThreads, 0);
-  if (per < 1) per = 1;
-  long long grid = static_cast<long long>(sms) * per;
-  if (grid > n_cells) grid = n_cells;
-  if (io_f64)
-    moments_kernel<double><<<int(grid), kMThreads, 0, st>>>(static_cast<const double*>(f), N, L, n_cells, eta0,
-                                                            delta0, mom, mask);
-  else
-    moments_kernel<float><<<int(grid), kMThreads, 0, st>>>(static_cast<const float*>(f), N, L, n_cells, eta0,
-                                                           delta0, mom, mask);
+  const int r = io_f64 ? launch_sums<double>(static_cast<const double*>(f), N, L, n_cells, mom, st)
+                       : launch_sums<float>(static_cast<const float*>(f), N, L, n_cells, mom, st);
+  if (r != 0) return r;
+  const long long blocks = (n_cells + kFinishThreads - 1) / kFinishThreads;
+  finish_kernel<<<static_cast<unsigned int>(blocks), kFinishThreads, 0, st>>>(N, L, n_cells, eta0, delta0, mom, mask);
   return int(cudaGetLastError());
 }
 
