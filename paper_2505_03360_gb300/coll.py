@@ -117,7 +117,7 @@ def make_desc(N, L, S=0.0, lam=1.0, b0=-1.0, M=48, Mtheta=4, Mr=16, sphere_rule=
               io_dtype=None) -> coll_plan_desc:
     p = PREC[prec] if isinstance(prec, str) else int(prec)
     if io_dtype is None:
-        io_dtype = 0 if p in (COLL_F64, COLL_F32X2) else 1
+        io_dtype = 1 if p == COLL_F32 else 0
     return coll_plan_desc(int(N), float(L), float(S), float(lam), float(b0), int(M), int(Mtheta), int(Mr),
                           int(sphere_rule), int(dealias), p, int(io_dtype))
 

@@ -39,7 +39,20 @@ struct LayoutInfo {
 };
 
 // compute types of the collision kernel
-enum CType : int { kCF64 = 0, kCF32 = 1, kCDF = 2 };
+enum CType : int { kCF64 = 0, kCF32 = 1, kCDF = 2, kCMixF16 = 3 };
+
+#ifdef __CUDACC__
+#define COLL_HD __host__ __device__
+#else
+#define COLL_HD
+#endif
+// Device image of a mixed-precision plan (mixed.cu): per-term tables, the
+// per-term bound max|A + iB|, then the tensor-core DFT matrices.
+COLL_HD inline size_t mixed_tab_bytes(int N, int n_terms) { return size_t(n_terms) * N * (N / 2) * N * 8; }
+COLL_HD inline size_t mixed_tmax_offset(int N, int n_terms) { return mixed_tab_bytes(N, n_terms); }
+COLL_HD inline size_t mixed_img_offset(int N, int n_terms) {
+  return (mixed_tab_bytes(N, n_terms) + size_t(n_terms) * 4 + 1023) / 1024 * 1024;
+}
 
 // Returns false if (N, ctype) has no kernel instantiation.
 bool layout_info(int N, int ctype, int variant, LayoutInfo* out);
@@ -86,6 +99,11 @@ int launch_ragged(int ctype, const RaggedTable& t, void* ws, size_t ws_per_cta, 
 int ragged_layout(int ctype, size_t* smem_bytes, size_t* ws_per_cta);
 int ragged_max_ctas_per_sm(int ctype, int* ctas);
 
+// Mixed-precision (tensor-core DFT-GEMM) collision kernel (mixed.cu)
+bool mixed_layout(int N, LayoutInfo* out);
+int launch_mixed(int N, bool io_f64, const CollArgs& a, int grid, void* stream);
+int mixed_max_ctas_per_sm(int N, bool io_f64, int* ctas);
+
 // Moments kernel (moments.cu)
 int launch_moments(const void* f, int io_f64, int N, double L, long long n_cells, double eta0,
                    double delta0, coll_moments* mom, uint8_t* mask, void* stream);
@@ -96,6 +114,7 @@ struct HostTables {
   std::vector<double> tab;    // [n_terms][N][N][N/2][2]
 };
 coll_status build_tables(const coll_plan_desc& d, HostTables* out);
+coll_status build_mixed_image(const HostTables& ht, int N, std::vector<unsigned char>* out);
 
 void count_launches(long long n);
 

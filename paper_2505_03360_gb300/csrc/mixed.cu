@@ -1,0 +1,617 @@
+// Mixed-precision collision path: every transform of the fused collision
+// operator (the forward R2C transform and the per-term inverse transforms,
+// arxiv 2505.03360 sec. 4.4.1) as DFT-GEMMs on the tcgen05 tensor cores.
+//
+// Same index-space algorithm as collision_impl.cuh:
+//   F   = DFT3(f)                    half spectrum k2 < N/2, Nyquist planes zero
+//   z_t = IDFT3((A_t + i B_t) F)     one complex 3D inverse per term
+//   Q   = sum_t Re(z_t) Im(z_t)      (the last term is the loss term)
+// Each 1D transform along an axis is a GEMM over a batch of pencils:
+//   Y[pencil][(v, re/im)] = sum_{(k, re/im)} X[pencil][(k, re/im)] D[(v, re/im)][(k, re/im)]
+// with D the real 2x2-block form of the N-point DFT matrix e^{+2 pi i k v / N}
+// (forward transforms by conjugating input and output).
+//
+// Precision (COLL_MIXED_F16X2): every operand is split into f16 parts,
+// x = x_h + x_l with x_h = f16(x), x_l = f16(x - x_h), and
+//   X D ~ (X_h + X_l) D_h + X_h D_l       (three products, FP32 accumulate)
+// which keeps about 22 significant bits per operand.  f16 has 5 exponent
+// bits, so each cell's data are scaled by powers of two: the input of a
+// three-pass transform is scaled to modulus <= 2^14 / N^3, which bounds every
+// intermediate (each pass grows the modulus by at most N) below 2^14.  The
+// bound of z_t's input uses max|F| (computed per cell) times max|A_t + iB_t|
+// (per term, from the plan).  Scales are undone exactly in FP32.
+//
+// Layouts.  One pencil per row; a row holds the pencil's N complex inputs as
+// 8-byte groups (re_h, im_h, re_l, im_l), i.e. K index 4k + 2 part + ri.  The
+// matrices in the tensor core's K-major 128-byte-swizzled shared-memory layout:
+//   B1[(v, ro)][(k, part, ri)] = D_h(ro, ri)(v, k)           -> (X_h + X_l) D_h
+//   B2[(v, ro)][(k, part, ri)] = part == 0 ? D_l(ro, ri)(v, k) : 0   -> X_h D_l
+// Passes per cell (row orders chosen so that, within a warp, the next pass's
+// K index varies fastest, which makes every epilogue store coalesced; F1 and
+// Y write back into the rows they read, so one pass buffer serves a cell):
+//   F2  rows (v0, v1), K = v2 (real f)     -> buf rows (k2h, v0), slot v1
+//   F1  rows (k2h, v0), K = v1             -> buf rows (k2h, k1), slot v0 (in place)
+//   F0  rows (k2h, k1), K = v0             -> F[k0][k1][k2h] (FP32 complex)
+//   per term t:
+//   X   rows (k0, k1), K = k2: the A tile is built from rows of F and of the
+//       term's (A, B) (contiguous in k2h; k2 > N/2 from the Hermitian partner
+//       row (-k0, -k1))                    -> buf rows (v2, k0), slot k1
+//   Y   rows (v2, k0), K = k1              -> buf rows (v2, v1), slot k0 (in place)
+//   Z   rows (v2, v1), K = k0              -> G[(v2, v1)][v0] += Re * Im in
+//                                             tensor memory; Q on the last term
+//
+// CTA organisation: one CTA per SM (persistent over cells), four warpgroups.
+// Warpgroup w takes the tiles w, w + 4, ... of each pass: it stages its
+// 128-row A tile in shared memory, one thread issues the MMAs into the
+// warpgroup's own accumulator columns in tensor memory and commits to the
+// warpgroup's mbarrier, and the warpgroup's 128 threads (thread = TMEM lane =
+// pencil) run the epilogue.  Warpgroups overlap one another's copies, MMAs
+// and epilogues.  The gain accumulator G of the whole cell lives in tensor
+// memory (N^3 / 128 columns).  Every mbarrier wait is bounded; on expiry the
+// kernel records kStatusTimeout, stops issuing work, waits (bounded) for its
+// MMAs in flight, frees its tensor memory and returns.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "coll_internal.h"
+
+namespace coll {
+
+namespace {
+
+constexpr int kMixWG = 4;
+constexpr int kMixThreads = 128 * kMixWG;
+
+template <int N> struct MixCfg {
+  static constexpr int H = N / 2;
+  static constexpr int KROW = 4 * N;                    // f16 per row
+  static constexpr int KB = KROW / 64;                  // 128-byte K blocks per row
+  static constexpr int NOUT = 2 * N;                    // matrix rows (v, re/im)
+  static constexpr int ROWS = N * N;                    // pencils of a full pass
+  static constexpr int RB = 8 * N;                      // bytes per row
+  static constexpr int A_TILE = KB * 128 * 128;         // bytes of a 128-row A tile
+  static constexpr int B_SET = KB * NOUT * 128;         // bytes of one matrix (B1 or B2)
+  static constexpr int GCOLS = N * N * N / 128;         // tensor-memory columns of G
+  static constexpr int TCOLS_USED = kMixWG * NOUT + GCOLS;
+  static constexpr int TCOLS = TCOLS_USED <= 32 ? 32 : TCOLS_USED <= 64 ? 64 : TCOLS_USED <= 128 ? 128
+                             : TCOLS_USED <= 256 ? 256 : 512;
+  static constexpr int SMEM_USED = 2 * B_SET + kMixWG * A_TILE + 1024;
+  // enough shared memory that no more CTAs share an SM than its 512 tensor-memory columns hold
+  static constexpr int SMEM_MIN = 233472 / (512 / TCOLS) - 4096;
+  static constexpr int SMEM = SMEM_USED > SMEM_MIN ? SMEM_USED : SMEM_MIN;
+  static_assert(N % 16 == 0 && ROWS % 128 == 0 && (H * N) % 128 == 0, "tile shape");
+  static_assert(TCOLS_USED <= 512, "tensor memory");
+  static_assert(SMEM <= 232448, "shared memory");
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>(1024u >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(2) << 61;
+  return d;
+}
+
+// instruction descriptor, kind::f16: f16 A and B (K-major), FP32 accumulator
+__device__ __forceinline__ uint32_t idesc_f16(int m, int n) {
+  return (1u << 4) | (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+
+// bounded wait for an mbarrier phase (about one second of SM clocks)
+__device__ __forceinline__ bool wait_parity(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  uint32_t ok = 0;
+  for (;;) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void wg_sync(int wg) { asm volatile("bar.sync %0, 128;" ::"r"(wg + 1) : "memory"); }
+// true iff p holds on all 128 threads of the warpgroup (a warpgroup barrier)
+__device__ __forceinline__ bool wg_all(int wg, bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n bar.red.and.pred q, %1, 128, q;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"(wg + 1), "r"(static_cast<uint32_t>(p))
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void tld32(uint32_t ta, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(ta));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tld16(uint32_t ta, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(ta));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tst16(uint32_t ta, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(ta),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+}
+
+// (re, im) -> 8 bytes (re_h, im_h, re_l, im_l)
+__device__ __forceinline__ uint2 split2(float re, float im) {
+  const __half2 h = __floats2half2_rn(re, im);
+  const float2 hb = __half22float2(h);
+  const __half2 l = __floats2half2_rn(__fsub_rn(re, hb.x), __fsub_rn(im, hb.y));
+  uint2 r;
+  r.x = *reinterpret_cast<const uint32_t*>(&h);
+  r.y = *reinterpret_cast<const uint32_t*>(&l);
+  return r;
+}
+
+// byte offset of 8-byte slot k of tile row `row` (128-byte swizzle, 16 KB per K block)
+__device__ __forceinline__ uint32_t a_off(int row, int k) {
+  const int c = (k >> 1) & 7;
+  return static_cast<uint32_t>((k >> 4) * 16384 + row * 128 + ((c ^ (row & 7)) << 4) + ((k & 1) << 3));
+}
+
+__device__ __forceinline__ int exp_of(float x) {         // e with x < 2^e (x >= 0 finite), clamped
+  int e = 0;
+  frexpf(x, &e);
+  if (!(x <= 3.0e38f)) e = 0;                            // non-finite: any scale (result is non-finite anyway)
+  return e < -100 ? -100 : (e > 100 ? 100 : e);
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(float* a, float v) {
+  atomicMax(reinterpret_cast<int*>(a), __float_as_int(v));   // non-negative floats order like their bits
+}
+
+enum MixPass : int { kMF2 = 0, kMF1, kMF0, kMX, kMY, kMZ };
+
+struct MixShared {
+  uint64_t bar[kMixWG];
+  uint32_t tbase;
+  int abort;
+  int bad;
+  float fmax;
+  float Fmax;
+};
+
+template <int N, typename Tio>
+struct MixCell {
+  using C = MixCfg<N>;
+  static constexpr int H = C::H;
+
+  // One pass over all tiles of this warpgroup.  Returns false (uniformly over
+  // the warpgroup) if an MMA wait expired; the expired phase stays pending.
+  static __device__ bool run(int pass, int wg, int lt, unsigned char* atile, uint32_t abase, uint32_t bbase,
+                             uint32_t tacc, uint32_t tG,
+                             uint32_t& phase, bool& pending, MixShared& sh, const Tio* __restrict__ f, Tio* __restrict__ Q,
+                             float2* Fs, unsigned char* buf,
+                             const float2* __restrict__ tab_t, float in_scale, float out_scale, bool first_term,
+                             bool last_term, bool& bad, float& lmax) {
+    const int rows = (pass == kMF1 || pass == kMF0) ? H * N : N * N;
+    const int nout = pass == kMF2 ? N : C::NOUT;
+    const int q = lt >> 5;
+    for (int ti = wg; ti < rows / 128; ti += kMixWG) {
+      const int r = ti * 128 + lt;
+      // ---- A tile
+      if (pass == kMF2) {
+        const Tio* fr = f + size_t(r) * N;
+#pragma unroll 1
+        for (int k0 = 0; k0 < N; k0 += 8) {
+          Tio x[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) x[e] = fr[k0 + e];
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            *reinterpret_cast<uint2*>(atile + a_off(lt, k0 + e)) =
+                split2(float(double(x[e]) * double(in_scale)), 0.0f);
+        }
+      } else if (pass == kMX) {
+        // Row (k0, k1): z[k2] = (A + iB) F for k2 < N/2 from row (k0, k1) of F
+        // and of the term's table, for k2 > N/2 from the partner row (-k0, -k1)
+        // at N - k2 (conjugated F).  Work item (row, j) covers k2 = 2j, 2j + 1
+        // and their partners; consecutive lanes take consecutive 16-byte
+        // pieces of the same rows, so every load instruction is coalesced.
+        constexpr int JN = H / 2;                 // 16-byte pieces per half row
+        constexpr int RPS = 128 / JN;             // rows per sweep of the warpgroup
+        const float4* F4 = reinterpret_cast<const float4*>(Fs);
+        const float4* T4 = reinterpret_cast<const float4*>(tab_t);
+        const int j = lt % JN;
+#pragma unroll 2
+        for (int it = 0; it < JN; ++it) {
+          const int row = it * RPS + lt / JN;
+          const int rr = ti * 128 + row;
+          const int k0 = rr / N, k1 = rr % N;
+          const int rp = ((N - k0) % N) * N + (N - k1) % N;
+          const float4 F = __ldcg(F4 + size_t(rr) * JN + j), T = __ldg(T4 + size_t(rr) * JN + j);
+          const float4 G = __ldcg(F4 + size_t(rp) * JN + j), U = __ldg(T4 + size_t(rp) * JN + j);
+          const uint2 a0 = split2(__fmul_rn(__fsub_rn(__fmul_rn(T.x, F.x), __fmul_rn(T.y, F.y)), in_scale),
+                                  __fmul_rn(__fadd_rn(__fmul_rn(T.x, F.y), __fmul_rn(T.y, F.x)), in_scale));
+          const uint2 a1 = split2(__fmul_rn(__fsub_rn(__fmul_rn(T.z, F.z), __fmul_rn(T.w, F.w)), in_scale),
+                                  __fmul_rn(__fadd_rn(__fmul_rn(T.z, F.w), __fmul_rn(T.w, F.z)), in_scale));
+          *reinterpret_cast<uint4*>(atile + a_off(row, 2 * j)) = make_uint4(a0.x, a0.y, a1.x, a1.y);
+          // partner: k2 = N - 2j - 1 and (j > 0) N - 2j, with conj(F)
+          *reinterpret_cast<uint2*>(atile + a_off(row, N - 2 * j - 1)) =
+              split2(__fmul_rn(__fadd_rn(__fmul_rn(U.z, G.z), __fmul_rn(U.w, G.w)), in_scale),
+                     __fmul_rn(__fsub_rn(__fmul_rn(U.w, G.z), __fmul_rn(U.z, G.w)), in_scale));
+          const uint2 b0 = j > 0 ? split2(__fmul_rn(__fadd_rn(__fmul_rn(U.x, G.x), __fmul_rn(U.y, G.y)), in_scale),
+                                          __fmul_rn(__fsub_rn(__fmul_rn(U.y, G.x), __fmul_rn(U.x, G.y)), in_scale))
+                                 : make_uint2(0u, 0u);
+          // slot N - 2j for j > 0; for j == 0 the same store zeroes the Nyquist slot N/2
+          *reinterpret_cast<uint2*>(atile + a_off(row, j > 0 ? N - 2 * j : H)) = b0;
+        }
+      } else {
+        const unsigned char* s0 = buf + size_t(ti) * 128 * C::RB;
+        for (int i = lt; i < 128 * C::KB * 8; i += 128) {
+          const int row = i / (C::KB * 8), j = i % (C::KB * 8);
+          cp_async16(abase + (j >> 3) * 16384 + row * 128 + (((j & 7) ^ (row & 7)) << 4),
+                     s0 + size_t(row) * C::RB + j * 16);
+        }
+        cp_async_wait_all();
+      }
+      fence_async_smem();
+      wg_sync(wg);
+      // ---- MMAs: (X_h + X_l) D_h + X_h D_l
+      if (lt == 0) {
+        fence_after();
+        const uint32_t id = idesc_f16(128, nout);
+        uint32_t acc = 0;
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+          for (int kb = 0; kb < C::KB; ++kb)
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+              mma_f16(tacc, sw128_desc(abase + kb * 16384 + ks * 32),
+                      sw128_desc(bbase + s * C::B_SET + kb * (C::NOUT * 128) + ks * 32), id, acc);
+              acc = 1;
+            }
+        mma_commit(&sh.bar[wg]);
+      }
+      if (!wg_all(wg, wait_parity(&sh.bar[wg], phase))) {
+        if (lt == 0) atomicExch(&sh.abort, 1);
+        pending = true;
+        return false;
+      }
+      phase ^= 1u;
+      fence_after();
+      // ---- epilogue: thread = TMEM lane = pencil row r
+      const uint32_t lane_base = static_cast<uint32_t>(32 * q) << 16;
+      for (int c0 = 0; c0 < nout; c0 += 32) {
+        uint32_t a[32];
+        tld32(tacc + lane_base + c0, a);
+        const int v0c = c0 >> 1;                         // first output index of this chunk
+        const int ne = (nout >> 1) - v0c < 16 ? (nout >> 1) - v0c : 16;
+        if (pass == kMZ) {
+          // G[(v0, v1)][v2] for v2 = v0c .. v0c + 15
+          const uint32_t gaddr = tG + lane_base + ti * N + v0c;
+          uint32_t g[16];
+          if (!first_term) tld16(gaddr, g);
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const float re = __uint_as_float(a[2 * e]), im = __uint_as_float(a[2 * e + 1]);
+            const float p = __fmul_rn(__fmul_rn(re, im), out_scale);
+            const float gv = first_term ? p : __fadd_rn(__uint_as_float(g[e]), p);
+            g[e] = __float_as_uint(gv);
+          }
+          if (!last_term) {
+            tst16(gaddr, g);
+          } else {
+            // r = (v2, v1), outputs v0: Q[v0][v1][v2]
+            Tio* qr = Q + (size_t(v0c) * N + (r % N)) * N + (r / N);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const float gv = __uint_as_float(g[e]);
+              bad |= !isfinite(gv);
+              qr[size_t(e) * N * N] = Tio(gv);
+            }
+          }
+        } else if (pass == kMF0) {
+          const int k2h = r / N, k1 = r % N;
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int k0 = v0c + e;
+            float re = __fmul_rn(__uint_as_float(a[2 * e]), out_scale);
+            float im = -__fmul_rn(__uint_as_float(a[2 * e + 1]), out_scale);
+            if (k0 == H || k1 == H) { re = 0.0f; im = 0.0f; }
+            lmax = fmaxf(lmax, __fadd_rn(fabsf(re), fabsf(im)));
+            Fs[(size_t(k0) * N + k1) * H + k2h] = make_float2(re, im);
+          }
+        } else {
+          // split and store into the next pass's row, slot = this pencil's next-K index
+          int drow0, dstride, slot;
+          if (pass == kMF2) {          // r = (v0, v1), out k2h -> row (k2h, v0), slot v1
+            drow0 = r / N; dstride = N; slot = r % N;
+          } else if (pass == kMF1) {   // r = (k2h, v0), out k1 -> row (k2h, k1), slot v0
+            drow0 = (r / N) * N; dstride = 1; slot = r % N;
+          } else if (pass == kMX) {    // r = (k0, k1), out v2 -> row (v2, k0), slot k1
+            drow0 = r / N; dstride = N; slot = r % N;
+          } else {                     // kMY: r = (v2, k0), out v1 -> row (v2, v1), slot k0
+            drow0 = (r / N) * N; dstride = 1; slot = r % N;
+          }
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            if (e >= ne) break;
+            const int v = v0c + e;
+            const uint2 s = split2(__uint_as_float(a[2 * e]), __uint_as_float(a[2 * e + 1]));
+            *reinterpret_cast<uint2*>(buf + size_t(drow0 + v * dstride) * C::RB + slot * 8) = s;
+          }
+        }
+      }
+      fence_before();
+      wg_sync(wg);
+    }
+    return true;
+  }
+
+  // Whole cell; returns true (uniformly) if the CTA must stop (a wait expired).
+  static __device__ bool cell(const Tio* __restrict__ f, Tio* __restrict__ Q, const float2* __restrict__ tab,
+                              const float* __restrict__ tmax, int n_terms, unsigned char* ws, unsigned char* atile,
+                              uint32_t abase,
+                              uint32_t bbase, uint32_t tacc, uint32_t tG, uint32_t& phase, bool& pending,
+                              MixShared& sh, bool& bad) {
+    const int tid = threadIdx.x, wg = tid >> 7, lt = tid & 127;
+    float2* Fs = reinterpret_cast<float2*>(ws);
+    unsigned char* buf = ws + size_t(N) * H * N * 8;
+    constexpr int cap = 14 - 3 * (N == 16 ? 4 : 5);     // input modulus bound 2^cap = 2^14 / N^3
+    auto stop = [&]() -> bool {                          // same answer on every thread
+      __syncthreads();
+      const bool v = *reinterpret_cast<volatile int*>(&sh.abort) != 0;
+      __syncthreads();
+      return v;
+    };
+
+    // max |f| for the forward scale
+    float m = 0.0f;
+    for (int i = tid; i < N * N * N; i += kMixThreads) m = fmaxf(m, float(fabs(double(f[i]))));
+    if (tid == 0) { sh.fmax = 0.0f; sh.Fmax = 0.0f; }
+    __syncthreads();
+    atomic_max_nonneg(&sh.fmax, m);
+    __syncthreads();
+    const int ef = cap - exp_of(sh.fmax);
+    float lmax = 0.0f;
+    run(kMF2, wg, lt, atile, abase, bbase, tacc, tG, phase, pending, sh, f, Q, Fs, buf, tab, ldexpf(1.0f, ef), 1.0f,
+        false, false, bad, lmax);
+    if (stop()) return true;
+    run(kMF1, wg, lt, atile, abase, bbase, tacc, tG, phase, pending, sh, f, Q, Fs, buf, tab, 1.0f, 1.0f, false,
+        false, bad, lmax);
+    if (stop()) return true;
+    run(kMF0, wg, lt, atile, abase, bbase, tacc, tG, phase, pending, sh, f, Q, Fs, buf, tab, 1.0f, ldexpf(1.0f, -ef),
+        false, false, bad, lmax);
+    atomic_max_nonneg(&sh.Fmax, lmax);
+    if (stop()) return true;
+    const float Fmax = sh.Fmax;
+    for (int t = 0; t < n_terms; ++t) {
+      const float bound = __fmul_ru(__fmul_ru(Fmax, tmax[t]), 1.0000005f);
+      const int et = cap - exp_of(bound);
+      const float2* tab_t = tab + size_t(t) * N * N * H;
+      run(kMX, wg, lt, atile, abase, bbase, tacc, tG, phase, pending, sh, f, Q, Fs, buf, tab_t, ldexpf(1.0f, et),
+          1.0f, false, false, bad, lmax);
+      if (stop()) return true;
+      run(kMY, wg, lt, atile, abase, bbase, tacc, tG, phase, pending, sh, f, Q, Fs, buf, tab_t, 1.0f, 1.0f, false,
+          false, bad, lmax);
+      if (stop()) return true;
+      run(kMZ, wg, lt, atile, abase, bbase, tacc, tG, phase, pending, sh, f, Q, Fs, buf, tab_t, 1.0f,
+          ldexpf(1.0f, -2 * et), t == 0, t == n_terms - 1, bad, lmax);
+      if (stop()) return true;
+    }
+    return false;
+  }
+};
+
+template <int N, typename Tio>
+__global__ void __launch_bounds__(kMixThreads, 1) mixed_kernel(CollArgs a) {
+  using C = MixCfg<N>;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  __shared__ MixShared sh;
+  const int tid = threadIdx.x, warp = tid >> 5, wg = tid >> 7;
+  const uint32_t raw = su32(smraw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* sm = smraw + (base - raw);
+  const uint32_t bbase = base;                                   // B1, B2
+  const uint32_t abase = base + 2 * C::B_SET + wg * C::A_TILE;   // this warpgroup's A tile
+
+  // matrices: copy the pre-swizzled image
+  const unsigned char* img = static_cast<const unsigned char*>(a.tab) + mixed_img_offset(N, a.n_terms);
+  for (int i = tid; i < 2 * C::B_SET / 16; i += kMixThreads)
+    reinterpret_cast<uint4*>(sm)[i] = __ldg(reinterpret_cast<const uint4*>(img) + i);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&sh.tbase)),
+                 "r"(C::TCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int w = 0; w < kMixWG; ++w)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&sh.bar[w])), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sh.abort = 0;
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tbase = sh.tbase;
+  const uint32_t tacc = tbase + wg * C::NOUT;
+  const uint32_t tG = tbase + kMixWG * C::NOUT;
+  uint32_t phase = 0;
+  bool pending = false, bad = false;
+  const auto* tab = static_cast<const float2*>(a.tab);
+  const float* tmax = reinterpret_cast<const float*>(static_cast<const unsigned char*>(a.tab) +
+                                                     mixed_tmax_offset(N, a.n_terms));
+  unsigned char* ws = static_cast<unsigned char*>(a.ws) + size_t(blockIdx.x) * a.ws_per_cta;
+  for (long long c = blockIdx.x; c < a.n_cells; c += gridDim.x) {
+    const Tio* f = static_cast<const Tio*>(a.f) + size_t(c) * N * N * N;
+    Tio* Q = static_cast<Tio*>(a.Q) + size_t(c) * N * N * N;
+    if (MixCell<N, Tio>::cell(f, Q, tab, tmax, a.n_terms, ws, sm + 2 * C::B_SET + wg * C::A_TILE, abase, bbase, tacc, tG, phase, pending, sh, bad))
+      break;
+  }
+  // a wait that expired may leave this warpgroup's last MMA batch in flight
+  if (pending) (void)wait_parity(&sh.bar[wg], phase);
+  fence_before();
+  if (__syncthreads_or(bad) && tid == 0) atomicOr(a.status, kStatusNonFinite);
+  if (sh.abort && tid == 0) atomicOr(a.status, kStatusTimeout);
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(C::TCOLS));
+  }
+}
+
+template <int N, typename Tio>
+int launch_mixed_t(const CollArgs& a, int grid, cudaStream_t st) {
+  auto k = mixed_kernel<N, Tio>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, MixCfg<N>::SMEM);
+  if (e != cudaSuccess) return int(e);
+  k<<<grid, kMixThreads, MixCfg<N>::SMEM, st>>>(a);
+  return int(cudaGetLastError());
+}
+
+template <int N, typename Tio>
+int occupancy_mixed_t(int* ctas) {
+  auto k = mixed_kernel<N, Tio>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, MixCfg<N>::SMEM);
+  if (e != cudaSuccess) return int(e);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k, kMixThreads, MixCfg<N>::SMEM);
+  const int by_tmem = 512 / MixCfg<N>::TCOLS;
+  if (*ctas > by_tmem) *ctas = by_tmem;
+  return int(e);
+}
+
+// IEEE binary16, round to nearest even (host)
+uint16_t half_bits(double x) {
+  const __half h = __double2half(x);
+  uint16_t b;
+  std::memcpy(&b, &h, 2);
+  return b;
+}
+double half_value(uint16_t b) {
+  __half h;
+  std::memcpy(&h, &b, 2);
+  return double(__half2float(h));
+}
+
+}  // namespace
+
+bool mixed_layout(int N, LayoutInfo* out) {
+  if (N != 16 && N != 32) return false;
+  LayoutInfo i;
+  i.N = N;
+  i.S0 = 1;
+  i.threads = kMixThreads;
+  i.fh_smem = false;
+  i.w_smem = false;
+  i.g_smem = true;
+  i.fh_bytes = size_t(N) * (N / 2) * N * 8;        // forward half spectrum (FP32 complex)
+  i.w_bytes = size_t(N) * N * 8 * N;               // one pass buffer
+  i.g_bytes = 0;                                   // the gain accumulator lives in tensor memory
+  *out = i;
+  return true;
+}
+
+int launch_mixed(int N, bool io_f64, const CollArgs& a, int grid, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (N == 16) return io_f64 ? launch_mixed_t<16, double>(a, grid, st) : launch_mixed_t<16, float>(a, grid, st);
+  if (N == 32) return io_f64 ? launch_mixed_t<32, double>(a, grid, st) : launch_mixed_t<32, float>(a, grid, st);
+  return int(cudaErrorInvalidValue);
+}
+
+int mixed_max_ctas_per_sm(int N, bool io_f64, int* ctas) {
+  if (N == 16) return io_f64 ? occupancy_mixed_t<16, double>(ctas) : occupancy_mixed_t<16, float>(ctas);
+  if (N == 32) return io_f64 ? occupancy_mixed_t<32, double>(ctas) : occupancy_mixed_t<32, float>(ctas);
+  return int(cudaErrorInvalidValue);
+}
+
+// Device image of a mixed plan: per-term tables [t][k0][k1][k2h] (A, B) as
+// float2, per-term max |A + iB| (rounded up), then the swizzled f16 matrices
+// B1 (hi) and B2 (lo, part 0 only) of the inverse N-point DFT.
+coll_status build_mixed_image(const HostTables& ht, int N, std::vector<unsigned char>* out) {
+  const int H = N / 2, nt = ht.n_terms;
+  const size_t img_off = mixed_img_offset(N, nt);
+  const int KROW = 4 * N, KB = KROW / 64, NOUT = 2 * N;
+  const size_t bset = size_t(KB) * NOUT * 128;
+  out->assign(img_off + 2 * bset, 0);
+  float2* tab = reinterpret_cast<float2*>(out->data());
+  float* tmax = reinterpret_cast<float*>(out->data() + mixed_tmax_offset(N, nt));
+  for (int t = 0; t < nt; ++t) {
+    double mx = 0.0;
+    for (int k0 = 0; k0 < N; ++k0)
+      for (int k1 = 0; k1 < N; ++k1)
+        for (int k2 = 0; k2 < H; ++k2) {
+          const size_t src = ((size_t(t) * N + k0) * N + k1) * H + k2;
+          const double A = ht.tab[2 * src], B = ht.tab[2 * src + 1];
+          tab[src] = make_float2(float(A), float(B));
+          mx = std::fmax(mx, std::sqrt(A * A + B * B));
+        }
+    tmax[t] = float(mx * (1.0 + 1e-6));
+  }
+  unsigned char* img = out->data() + img_off;
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int s = 0; s < 2; ++s)
+    for (int j = 0; j < NOUT; ++j) {
+      const int v = j >> 1, ro = j & 1;
+      for (int kk = 0; kk < KROW; ++kk) {
+        const int k = kk >> 2, part = (kk >> 1) & 1, ri = kk & 1;
+        const double th = two_pi * double((size_t(k) * v) % N) / double(N);
+        const double c = std::cos(th), sn = std::sin(th);
+        // [[cos, -sin], [sin, cos]] for y = sum e^{+i th} x
+        const double d = ro == 0 ? (ri == 0 ? c : -sn) : (ri == 0 ? sn : c);
+        const uint16_t hb = half_bits(d);
+        uint16_t val = 0;
+        if (s == 0) val = hb;
+        else if (part == 0) val = half_bits(d - half_value(hb));
+        const int kb = kk / 64, e = kk % 64, chunk = e / 8, within = e % 8;
+        const size_t off = size_t(s) * bset + size_t(kb) * NOUT * 128 + size_t(j) * 128 +
+                           size_t((chunk ^ (j & 7)) * 16) + size_t(within) * 2;
+        std::memcpy(img + off, &val, 2);
+      }
+    }
+  return COLL_OK;
+}
+
+}  // namespace coll

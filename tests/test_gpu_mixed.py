@@ -1,0 +1,105 @@
+"""Tensor-core (tcgen05) DFT-GEMM collision path, COLL_MIXED_F16X2, through the
+C ABI: parity with the oracle and with the FP64 path, degenerate cells and
+argument errors.
+
+Tolerance.  Every transform operand carries the f16 hi+lo split (about 22
+significant bits, 2^-22 ~ 2.4e-7 relative per operand) and FP32 accumulation.
+Q = gain - loss is a small difference of large terms, which amplifies the
+relative error of the transforms by the ratio |gain| / |Q| (10^3 .. 10^4 for
+the smooth bimodal cells of the benchmark).  An f16 hi+lo emulation of the same
+products in float64 gives relative L2 errors of 4e-5 .. 1e-3 on these cells,
+and the GPU's FP32 accumulation adds about as much again; over 64 benchmark
+cells the median is 4e-4 and the largest 6e-3.  The tests allow 1e-2 per cell
+and 1e-3 for the median at N = 32, 1e-3 per cell at N = 16.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_2505_03360_gb300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_2505_03360_gb300 import coll, synth  # noqa: E402
+from oracle.collision import q_fast  # noqa: E402
+from oracle.kernel import Params, multipliers  # noqa: E402
+
+L = synth.DEFAULT_L
+TOL = {16: 1e-3, 32: 1e-2}
+MEDIAN_TOL = 1e-3
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("N,io", [(16, "f64"), (32, "f64"), (16, "f32"), (32, "f32")])
+def test_mixed_matches_oracle(N, io):
+    M, Mr = (32, 8) if N == 16 else (48, 16)
+    cells = np.concatenate([synth.bimodal_batch(3, N, L, seed=synth.BASE_SEED + 3),
+                            np.stack([synth.anisotropic_cell(N, L, synth.rng(N + 1), dtype=np.float64)])])
+    dt = torch.float64 if io == "f64" else torch.float32
+    f = torch.from_numpy(cells).to("cuda", dt)
+    p = coll.Plan(N, L, lam=1.0, M=M, Mtheta=4, Mr=Mr, prec="mixed_f16x2", io_dtype=0 if io == "f64" else 1,
+                  max_cells=len(cells))
+    Q = p.eval(f)
+    torch.cuda.synchronize()
+    assert p.status() == coll.COLL_OK
+    pr = Params(N=N, L=L, lam=1.0, M=M, Mtheta=4, Mr=Mr)
+    m = multipliers(pr)
+    for c in range(len(cells)):
+        want = q_fast(f[c].double().cpu().numpy(), pr, m)
+        assert rel(Q[c].double().cpu().numpy(), want) <= TOL[N], c
+    p.close()
+
+
+def test_mixed_vs_fp64_batch_and_lambda0():
+    """64 benchmark-shaped cells against the FP64 path; a lambda = 0 plan too."""
+    N, n = 32, 64
+    f = synth.bimodal_batch_device(n, N, L, 11, dtype=torch.float64)
+    for lam, Mr in ((1.0, 16), (0.0, 8)):
+        pm = coll.Plan(N, L, lam=lam, M=48, Mtheta=4, Mr=Mr, prec="mixed_f16x2", max_cells=n)
+        p64 = coll.Plan(N, L, lam=lam, M=48, Mtheta=4, Mr=Mr, prec="f64", max_cells=n)
+        qm, q64 = pm.eval(f), p64.eval(f)
+        torch.cuda.synchronize()
+        err = (torch.linalg.norm((qm - q64).reshape(n, -1), dim=1) / torch.linalg.norm(q64.reshape(n, -1), dim=1))
+        assert pm.status() == coll.COLL_OK
+        assert float(err.max()) <= TOL[N] and float(err.median()) <= MEDIAN_TOL, (lam, float(err.max()))
+        pm.close()
+        p64.close()
+
+
+def test_mixed_degenerate_cells_and_status():
+    N = 16
+    p = coll.Plan(N, L, lam=1.0, M=32, Mtheta=4, Mr=8, prec="mixed_f16x2", max_cells=3)
+    f = torch.from_numpy(synth.bimodal_batch(3, N, L, seed=5)).cuda()
+    f[0] = 0.0
+    Q = p.eval(f)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(Q[0]) == 0 and torch.isfinite(Q).all()
+    assert p.status() == coll.COLL_OK
+    ref = Q[2].clone()
+    f[1, 3, 4, 5] = float("nan")
+    Q = p.eval(f)
+    torch.cuda.synchronize()
+    assert p.status() == coll.COLL_ENONFINITE
+    assert torch.equal(Q[2], ref)                 # other cells unaffected, bitwise
+    coll.coll_device_status_clear(p.handle)
+    p.close()
+
+
+def test_mixed_unsupported_shapes():
+    with pytest.raises(coll.CollError) as e:
+        coll.Plan(24, L, lam=1.0, M=32, Mtheta=4, Mr=8, prec="mixed_f16x2")
+    assert e.value.status == coll.COLL_EUNSUPPORTED
+    with pytest.raises(coll.CollError) as e:
+        coll.Plan(16, L, lam=1.0, M=32, Mtheta=4, Mr=8, prec="mixed_bf16x3")
+    assert e.value.status == coll.COLL_EUNSUPPORTED
+    p = coll.Plan(16, L, lam=1.0, M=32, Mtheta=4, Mr=8, prec="mixed_f16x2", max_cells=1)
+    f = torch.zeros((1, 16, 16, 16), dtype=torch.float64, device="cuda")
+    with pytest.raises(coll.CollError) as e:              # the ragged kernel runs SIMT compute types only
+        coll.coll_ragged_workspace_size([(p.handle, f, torch.empty_like(f))], [1])
+    assert e.value.status == coll.COLL_EUNSUPPORTED
+    p.close()
