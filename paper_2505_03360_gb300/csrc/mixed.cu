@@ -22,10 +22,11 @@
 // (per term, from the plan).  Scales are undone exactly in FP32.
 //
 // Layouts.  One pencil per row; a row holds the pencil's N complex inputs as
-// 8-byte groups (re_h, im_h, re_l, im_l), i.e. K index 4k + 2 part + ri.  The
-// matrices in the tensor core's K-major 128-byte-swizzled shared-memory layout:
-//   B1[(v, ro)][(k, part, ri)] = D_h(ro, ri)(v, k)           -> (X_h + X_l) D_h
-//   B2[(v, ro)][(k, part, ri)] = part == 0 ? D_l(ro, ri)(v, k) : 0   -> X_h D_l
+// all hi parts, then all lo parts: K index 2N part + 2k + ri (f16 pairs
+// (re, im) per element and part).  The matrices, in the tensor core's K-major
+// 128-byte-swizzled shared-memory layout:
+//   B1[(v, ro)][(part, k, ri)] = D_h(ro, ri)(v, k)    over all 4N K  -> (X_h + X_l) D_h
+//   B2[(v, ro)][(k, ri)]       = D_l(ro, ri)(v, k)    over the first 2N K (the hi parts) -> X_h D_l
 // Passes per cell (row orders chosen so that, within a warp, the next pass's
 // K index varies fastest, which makes every epilogue store coalesced; F1 and
 // Y write back into the rows they read, so one pass buffer serves a cell):
@@ -74,17 +75,21 @@ template <int N> struct MixCfg {
   static constexpr int ROWS = N * N;                    // pencils of a full pass
   static constexpr int RB = 8 * N;                      // bytes per row
   static constexpr int A_TILE = KB * 128 * 128;         // bytes of a 128-row A tile
-  static constexpr int B_SET = KB * NOUT * 128;         // bytes of one matrix (B1 or B2)
+  static constexpr int KB2 = (2 * N + 63) / 64;         // K blocks of B2 (hi parts only)
+  static constexpr int B1_SET = KB * NOUT * 128;        // bytes of B1
+  static constexpr int B2_SET = KB2 * NOUT * 128;       // bytes of B2
+  static constexpr int B_SETS = B1_SET + B2_SET;
   static constexpr int GCOLS = N * N * N / 128;         // tensor-memory columns of G
   static constexpr int TCOLS_USED = kMixWG * NOUT + GCOLS;
   static constexpr int TCOLS = TCOLS_USED <= 32 ? 32 : TCOLS_USED <= 64 ? 64 : TCOLS_USED <= 128 ? 128
                              : TCOLS_USED <= 256 ? 256 : 512;
-  static constexpr int SMEM_USED = 2 * B_SET + kMixWG * A_TILE + 1024;
+  static constexpr int SMEM_USED = B_SETS + kMixWG * A_TILE + 1024;
   // enough shared memory that no more CTAs share an SM than its 512 tensor-memory columns hold
   static constexpr int SMEM_MIN = 233472 / (512 / TCOLS) - 4096;
   static constexpr int SMEM = SMEM_USED > SMEM_MIN ? SMEM_USED : SMEM_MIN;
   static_assert(N % 16 == 0 && ROWS % 128 == 0 && (H * N) % 128 == 0, "tile shape");
   static_assert(TCOLS_USED <= 512, "tensor memory");
+  static_assert(B_SETS % 1024 == 0, "A tiles 1024-byte aligned");
   static_assert(SMEM <= 232448, "shared memory");
 };
 
@@ -194,10 +199,9 @@ __device__ __forceinline__ uint2 split2(float re, float im) {
   return r;
 }
 
-// byte offset of 8-byte slot k of tile row `row` (128-byte swizzle, 16 KB per K block)
-__device__ __forceinline__ uint32_t a_off(int row, int k) {
-  const int c = (k >> 1) & 7;
-  return static_cast<uint32_t>((k >> 4) * 16384 + row * 128 + ((c ^ (row & 7)) << 4) + ((k & 1) << 3));
+// shared-memory offset of byte b of tile row `row` (128-byte swizzle, 16 KB per K block)
+__device__ __forceinline__ uint32_t a_off(int row, int b) {
+  return static_cast<uint32_t>((b >> 7) * 16384 + row * 128 + ((((b >> 4) & 7) ^ (row & 7)) << 4) + (b & 15));
 }
 
 __device__ __forceinline__ int exp_of(float x) {         // e with x < 2^e (x >= 0 finite), clamped
@@ -244,14 +248,16 @@ struct MixCell {
       if (pass == kMF2) {
         const Tio* fr = f + size_t(r) * N;
 #pragma unroll 1
-        for (int k0 = 0; k0 < N; k0 += 8) {
-          Tio x[8];
+        for (int k0 = 0; k0 < N; k0 += 4) {
+          uint32_t h[4], l[4];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) x[e] = fr[k0 + e];
-#pragma unroll
-          for (int e = 0; e < 8; ++e)
-            *reinterpret_cast<uint2*>(atile + a_off(lt, k0 + e)) =
-                split2(float(double(x[e]) * double(in_scale)), 0.0f);
+          for (int e = 0; e < 4; ++e) {
+            const uint2 v = split2(float(double(fr[k0 + e]) * double(in_scale)), 0.0f);
+            h[e] = v.x;
+            l[e] = v.y;
+          }
+          *reinterpret_cast<uint4*>(atile + a_off(lt, 4 * k0)) = make_uint4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<uint4*>(atile + a_off(lt, 4 * N + 4 * k0)) = make_uint4(l[0], l[1], l[2], l[3]);
         }
       } else if (pass == kMX) {
         // Row (k0, k1): z[k2] = (A + iB) F for k2 < N/2 from row (k0, k1) of F
@@ -276,16 +282,21 @@ struct MixCell {
                                   __fmul_rn(__fadd_rn(__fmul_rn(T.x, F.y), __fmul_rn(T.y, F.x)), in_scale));
           const uint2 a1 = split2(__fmul_rn(__fsub_rn(__fmul_rn(T.z, F.z), __fmul_rn(T.w, F.w)), in_scale),
                                   __fmul_rn(__fadd_rn(__fmul_rn(T.z, F.w), __fmul_rn(T.w, F.z)), in_scale));
-          *reinterpret_cast<uint4*>(atile + a_off(row, 2 * j)) = make_uint4(a0.x, a0.y, a1.x, a1.y);
+          *reinterpret_cast<uint2*>(atile + a_off(row, 8 * j)) = make_uint2(a0.x, a1.x);
+          *reinterpret_cast<uint2*>(atile + a_off(row, 4 * N + 8 * j)) = make_uint2(a0.y, a1.y);
           // partner: k2 = N - 2j - 1 and (j > 0) N - 2j, with conj(F)
-          *reinterpret_cast<uint2*>(atile + a_off(row, N - 2 * j - 1)) =
-              split2(__fmul_rn(__fadd_rn(__fmul_rn(U.z, G.z), __fmul_rn(U.w, G.w)), in_scale),
-                     __fmul_rn(__fsub_rn(__fmul_rn(U.w, G.z), __fmul_rn(U.z, G.w)), in_scale));
+          const uint2 b1 = split2(__fmul_rn(__fadd_rn(__fmul_rn(U.z, G.z), __fmul_rn(U.w, G.w)), in_scale),
+                                  __fmul_rn(__fsub_rn(__fmul_rn(U.w, G.z), __fmul_rn(U.z, G.w)), in_scale));
+          const int k2b = N - 2 * j - 1;
+          *reinterpret_cast<uint32_t*>(atile + a_off(row, 4 * k2b)) = b1.x;
+          *reinterpret_cast<uint32_t*>(atile + a_off(row, 4 * N + 4 * k2b)) = b1.y;
           const uint2 b0 = j > 0 ? split2(__fmul_rn(__fadd_rn(__fmul_rn(U.x, G.x), __fmul_rn(U.y, G.y)), in_scale),
                                           __fmul_rn(__fsub_rn(__fmul_rn(U.y, G.x), __fmul_rn(U.x, G.y)), in_scale))
                                  : make_uint2(0u, 0u);
           // slot N - 2j for j > 0; for j == 0 the same store zeroes the Nyquist slot N/2
-          *reinterpret_cast<uint2*>(atile + a_off(row, j > 0 ? N - 2 * j : H)) = b0;
+          const int k2a = j > 0 ? N - 2 * j : H;
+          *reinterpret_cast<uint32_t*>(atile + a_off(row, 4 * k2a)) = b0.x;
+          *reinterpret_cast<uint32_t*>(atile + a_off(row, 4 * N + 4 * k2a)) = b0.y;
         }
       } else {
         const unsigned char* s0 = buf + size_t(ti) * 128 * C::RB;
@@ -304,15 +315,15 @@ struct MixCell {
         const uint32_t id = idesc_f16(128, nout);
         uint32_t acc = 0;
 #pragma unroll
-        for (int s = 0; s < 2; ++s)
+        for (int kk = 0; kk < C::KB * 4; ++kk) {          // B1 over all 4N K: (X_h + X_l) D_h
+          mma_f16(tacc, sw128_desc(abase + (kk >> 2) * 16384 + (kk & 3) * 32),
+                  sw128_desc(bbase + (kk >> 2) * (C::NOUT * 128) + (kk & 3) * 32), id, acc);
+          acc = 1;
+        }
 #pragma unroll
-          for (int kb = 0; kb < C::KB; ++kb)
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-              mma_f16(tacc, sw128_desc(abase + kb * 16384 + ks * 32),
-                      sw128_desc(bbase + s * C::B_SET + kb * (C::NOUT * 128) + ks * 32), id, acc);
-              acc = 1;
-            }
+        for (int kk = 0; kk < 2 * N / 16; ++kk)           // B2 over the hi parts: X_h D_l
+          mma_f16(tacc, sw128_desc(abase + (kk >> 2) * 16384 + (kk & 3) * 32),
+                  sw128_desc(bbase + C::B1_SET + (kk >> 2) * (C::NOUT * 128) + (kk & 3) * 32), id, 1u);
         mma_commit(&sh.bar[wg]);
       }
       if (!wg_all(wg, wait_parity(&sh.bar[wg], phase))) {
@@ -381,7 +392,9 @@ struct MixCell {
             if (e >= ne) break;
             const int v = v0c + e;
             const uint2 s = split2(__uint_as_float(a[2 * e]), __uint_as_float(a[2 * e + 1]));
-            *reinterpret_cast<uint2*>(buf + size_t(drow0 + v * dstride) * C::RB + slot * 8) = s;
+            unsigned char* rowp = buf + size_t(drow0 + v * dstride) * C::RB;
+            *reinterpret_cast<uint32_t*>(rowp + slot * 4) = s.x;
+            *reinterpret_cast<uint32_t*>(rowp + 4 * N + slot * 4) = s.y;
           }
         }
       }
@@ -456,11 +469,11 @@ __global__ void __launch_bounds__(kMixThreads, 1) mixed_kernel(CollArgs a) {
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* sm = smraw + (base - raw);
   const uint32_t bbase = base;                                   // B1, B2
-  const uint32_t abase = base + 2 * C::B_SET + wg * C::A_TILE;   // this warpgroup's A tile
+  const uint32_t abase = base + C::B_SETS + wg * C::A_TILE;       // this warpgroup's A tile
 
   // matrices: copy the pre-swizzled image
   const unsigned char* img = static_cast<const unsigned char*>(a.tab) + mixed_img_offset(N, a.n_terms);
-  for (int i = tid; i < 2 * C::B_SET / 16; i += kMixThreads)
+  for (int i = tid; i < C::B_SETS / 16; i += kMixThreads)
     reinterpret_cast<uint4*>(sm)[i] = __ldg(reinterpret_cast<const uint4*>(img) + i);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&sh.tbase)),
@@ -489,7 +502,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) mixed_kernel(CollArgs a) {
   for (long long c = blockIdx.x; c < a.n_cells; c += gridDim.x) {
     const Tio* f = static_cast<const Tio*>(a.f) + size_t(c) * N * N * N;
     Tio* Q = static_cast<Tio*>(a.Q) + size_t(c) * N * N * N;
-    if (MixCell<N, Tio>::cell(f, Q, tab, tmax, a.n_terms, ws, sm + 2 * C::B_SET + wg * C::A_TILE, abase, bbase, tacc, tG, phase, pending, sh, bad))
+    if (MixCell<N, Tio>::cell(f, Q, tab, tmax, a.n_terms, ws, sm + C::B_SETS + wg * C::A_TILE, abase, bbase, tacc, tG, phase, pending, sh, bad))
       break;
   }
   // a wait that expired may leave this warpgroup's last MMA batch in flight
@@ -569,13 +582,14 @@ int mixed_max_ctas_per_sm(int N, bool io_f64, int* ctas) {
 
 // Device image of a mixed plan: per-term tables [t][k0][k1][k2h] (A, B) as
 // float2, per-term max |A + iB| (rounded up), then the swizzled f16 matrices
-// B1 (hi) and B2 (lo, part 0 only) of the inverse N-point DFT.
+// B1 (hi, applied to both parts of the operand) and B2 (lo, applied to the hi
+// parts) of the inverse N-point DFT.
 coll_status build_mixed_image(const HostTables& ht, int N, std::vector<unsigned char>* out) {
   const int H = N / 2, nt = ht.n_terms;
   const size_t img_off = mixed_img_offset(N, nt);
-  const int KROW = 4 * N, KB = KROW / 64, NOUT = 2 * N;
-  const size_t bset = size_t(KB) * NOUT * 128;
-  out->assign(img_off + 2 * bset, 0);
+  const int KROW = 4 * N, KB = KROW / 64, KB2 = (2 * N + 63) / 64, NOUT = 2 * N;
+  const size_t b1 = size_t(KB) * NOUT * 128, b2 = size_t(KB2) * NOUT * 128;
+  out->assign(img_off + b1 + b2, 0);
   float2* tab = reinterpret_cast<float2*>(out->data());
   float* tmax = reinterpret_cast<float*>(out->data() + mixed_tmax_offset(N, nt));
   for (int t = 0; t < nt; ++t) {
@@ -592,25 +606,26 @@ coll_status build_mixed_image(const HostTables& ht, int N, std::vector<unsigned 
   }
   unsigned char* img = out->data() + img_off;
   const double two_pi = 6.283185307179586476925286766559;
-  for (int s = 0; s < 2; ++s)
-    for (int j = 0; j < NOUT; ++j) {
-      const int v = j >> 1, ro = j & 1;
-      for (int kk = 0; kk < KROW; ++kk) {
-        const int k = kk >> 2, part = (kk >> 1) & 1, ri = kk & 1;
-        const double th = two_pi * double((size_t(k) * v) % N) / double(N);
-        const double c = std::cos(th), sn = std::sin(th);
-        // [[cos, -sin], [sin, cos]] for y = sum e^{+i th} x
-        const double d = ro == 0 ? (ri == 0 ? c : -sn) : (ri == 0 ? sn : c);
-        const uint16_t hb = half_bits(d);
-        uint16_t val = 0;
-        if (s == 0) val = hb;
-        else if (part == 0) val = half_bits(d - half_value(hb));
-        const int kb = kk / 64, e = kk % 64, chunk = e / 8, within = e % 8;
-        const size_t off = size_t(s) * bset + size_t(kb) * NOUT * 128 + size_t(j) * 128 +
-                           size_t((chunk ^ (j & 7)) * 16) + size_t(within) * 2;
-        std::memcpy(img + off, &val, 2);
-      }
+  auto put = [&](size_t region, int j, int kk, uint16_t val) {     // swizzled K-major position
+    const int kb = kk / 64, e = kk % 64, chunk = e / 8, within = e % 8;
+    const size_t off = region + size_t(kb) * NOUT * 128 + size_t(j) * 128 + size_t((chunk ^ (j & 7)) * 16) +
+                       size_t(within) * 2;
+    std::memcpy(img + off, &val, 2);
+  };
+  for (int j = 0; j < NOUT; ++j) {
+    const int v = j >> 1, ro = j & 1;
+    for (int kk = 0; kk < 2 * N; ++kk) {
+      const int k = kk >> 1, ri = kk & 1;
+      const double th = two_pi * double((size_t(k) * v) % N) / double(N);
+      const double c = std::cos(th), sn = std::sin(th);
+      // [[cos, -sin], [sin, cos]] for y = sum e^{+i th} x
+      const double d = ro == 0 ? (ri == 0 ? c : -sn) : (ri == 0 ? sn : c);
+      const uint16_t hb = half_bits(d);
+      put(0, j, kk, hb);                 // B1, hi parts
+      put(0, j, 2 * N + kk, hb);         // B1, lo parts
+      put(b1, j, kk, half_bits(d - half_value(hb)));   // B2
     }
+  }
   return COLL_OK;
 }
 
