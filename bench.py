@@ -52,7 +52,28 @@ def fp64_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
 KERNEL_SOURCES = {
     "collision_f64_n32": ["collision_impl.cuh", "collision_layout.cuh", "fft.cuh", "twiddles.h", "coll_inst_d32.cu"],
     "moments_f64": ["moments.cu"],
+    "mixed_f16_n32": ["mixed.cu"],
 }
+
+
+def mixed_mma_flops_per_cell(N: int, n_terms: int) -> float:
+    """Executed tensor-core flops of the f16 hi+lo DFT-GEMM path per cell: 128-row
+    tiles; per tile (4N/16) K steps against the hi matrix and (2N/16) against
+    the lo matrix, each 2 * 128 * n_out * 16 flops (n_out = 2N, N for the real
+    first forward pass)."""
+    steps = 4 * N // 16 + 2 * N // 16
+    per = lambda nout: steps * 2.0 * 128 * nout * 16
+    tiles_f2 = N * N // 128
+    tiles_full = 2 * (N // 2) * N // 128 + 3 * n_terms * N * N // 128
+    return tiles_f2 * per(N) + tiles_full * per(2 * N)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p))
+    except Exception:
+        return {}
 
 
 def src_hash(kernel_key: str) -> str:
@@ -217,6 +238,8 @@ def run_ours(args, rank, world, local_rank):
             ev[1].record(stream)
         coll.moments_realizability(f, 0 if f.dtype == torch.float64 else 1, N, w["L"], n, w["eta0"], w["delta0"],
                                    mom, mask, stream=stream)
+        if ev is not None:
+            ev[2].record(stream)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -224,7 +247,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(args.steps)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = coll.coll_launch_count()
     with ClockSampler(_smi_id(torch, dev, local_rank)) as clk:
@@ -236,7 +259,8 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize(dev)
     launches = coll.coll_launch_count() - launches0
     elapsed = t_start.elapsed_time(t_end) / 1e3
-    coll_ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    coll_ms = sum(a.elapsed_time(b) for a, b, _ in evs) / args.steps
+    mom_ms = sum(b.elapsed_time(c) for _, b, c in evs) / args.steps
     assert plan.status() == coll.COLL_OK
     if world > 1:
         t = torch.tensor([elapsed], device=dev)
@@ -315,6 +339,28 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     t32 = a32.elapsed_time(b32) / 1e3 / args.steps
     err32 = float(torch.linalg.vector_norm(Q32.double() - Q) / torch.linalg.vector_norm(Q))
+    del Q32, f32
+
+    # tensor-core DFT-GEMM variant (f16 hi+lo split, FP32 accumulate) on the same FP64 cells
+    Qm = torch.empty_like(f)
+    planm = coll.Plan(N, w["L"], lam=w["lam"], M=w["M"], Mtheta=w["Mtheta"], Mr=w["Mr"], prec="mixed_f16x2",
+                      io_dtype=0, max_cells=n, device=dev)
+    wsm = planm.reserve(n)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            coll.coll_eval_batch(planm.handle, f, Qm, n, wsm, stream=stream)
+    torch.cuda.synchronize(dev)
+    am, bm = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    am.record(stream)
+    for _ in range(args.steps):
+        coll.coll_eval_batch(planm.handle, f, Qm, n, wsm, stream=stream)
+    bm.record(stream)
+    torch.cuda.synchronize(dev)
+    tm = am.elapsed_time(bm) / 1e3 / args.steps
+    assert planm.status() == coll.COLL_OK
+    cell_err = torch.linalg.vector_norm((Qm - Q).reshape(n, -1), dim=1) / torch.linalg.vector_norm(Q.reshape(n, -1), dim=1)
+    errm = float(torch.linalg.vector_norm(Qm - Q) / torch.linalg.vector_norm(Q))
+    del Qm
 
     if rank != 0:
         return
@@ -327,6 +373,10 @@ def run_ours(args, rank, world, local_rank):
     sm_for_peak = 2070.0
     peak = fp64_peak_tflops(sm_for_peak)
     traffic = load_traffic("collision_f64_n32")
+    peaks = measured_peaks()
+    tc_peak = peaks.get("bf16_tflops")
+    mma_flops = mixed_mma_flops_per_cell(N, planm.n_terms) * n
+    mom_bytes = f.numel() * 8 + mom.numel() * 8 + mask.numel()
     e2e_bytes_in = f.numel() * 8
     e2e_bytes_out = Q.numel() * 8 + mom.numel() * 8 + mask.numel()
     line = {
@@ -349,7 +399,23 @@ def run_ours(args, rank, world, local_rank):
         "variants": {"f32x2": {"value": n / tx, "unit": "cell-evals/s", "rel_l2_vs_f64": errx,
                                "ms_per_launch": 1e3 * tx, "arithmetic": "float pairs (~48 bits) on the FP32 pipe"},
                      "f32": {"value": n / t32, "unit": "cell-evals/s", "rel_l2_vs_f64": err32,
-                             "ms_per_launch": 1e3 * t32}},
+                             "ms_per_launch": 1e3 * t32},
+                     "mixed_f16x2": {
+                         "value": n / tm, "unit": "cell-evals/s", "rel_l2_vs_f64": errm,
+                         "cell_rel_l2_median": float(cell_err.median()), "cell_rel_l2_max": float(cell_err.max()),
+                         "ms_per_launch": 1e3 * tm, "speedup_vs_f64": coll_ms / (1e3 * tm),
+                         "arithmetic": "DFT-GEMMs on tcgen05 tensor cores, f16 hi+lo operands, FP32 accumulate",
+                         "roofline": {"bound": "tensor", "achieved": mma_flops / tm / 1e12, "peak": tc_peak,
+                                      "unit": "TFLOP/s",
+                                      "frac": (mma_flops / tm / 1e12 / tc_peak) if tc_peak else None,
+                                      "peak_basis": "measured dense bf16 burst (f16 runs at the same dense rate)",
+                                      "executed_mma_flops_per_launch": mma_flops,
+                                      "traffic": load_traffic("mixed_f16_n32"),
+                                      "algorithmic_tflops": flops / tm / 1e12}}},
+        "moments": {"kernel": "moments sums + scalar finish (2 launches)", "ms_per_launch": mom_ms,
+                    "achieved_gbs": mom_bytes / (mom_ms / 1e3) / 1e9, "peak_gbs": peaks.get("hbm_gbs"),
+                    "frac": (mom_bytes / (mom_ms / 1e3) / 1e9 / peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None,
+                    "bytes_per_launch": mom_bytes, "bound": "hbm", "traffic": load_traffic("moments_f64")},
     }
     if args.serve_requests > 0:
         from paper_2505_03360_gb300.service import Service, stream_jobs
@@ -374,6 +440,7 @@ def run_ours(args, rank, world, local_rank):
     plan.close()
     plan32.close()
     planx.close()
+    planm.close()
 
 
 def main():
@@ -390,7 +457,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=100,
                     help="requests of the serving stream measured beside the main line (0: skip)")
     ap.add_argument("--serve-max-cells", type=int, default=64)
-    ap.add_argument("--prec", default="f64", choices=["f64", "f32x2", "f32"],
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32x2", "f32", "mixed_f16x2"],
                     help="compute precision of the main path in --profile-only runs")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
