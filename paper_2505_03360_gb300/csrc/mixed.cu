@@ -184,11 +184,10 @@ __device__ __forceinline__ void tst16(uint32_t ta, const uint32_t (&v)[16]) {
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
-}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// (re, im) -> 8 bytes (re_h, im_h, re_l, im_l)
+// (re, im) -> (hi pair, lo pair) as two packed f16x2 words: hi = f16(x),
+// lo = f16(x - hi) (x - hi exact in FP32)
 __device__ __forceinline__ uint2 split2(float re, float im) {
   const __half2 h = __floats2half2_rn(re, im);
   const float2 hb = __half22float2(h);
@@ -231,21 +230,33 @@ struct MixCell {
   using C = MixCfg<N>;
   static constexpr int H = C::H;
 
+  // cp.async of 128 rows (tile ti of the pass buffer) into the swizzled A tile
+  static __device__ __forceinline__ void load_tile(const unsigned char* buf, int ti, int lt, uint32_t abase) {
+    const unsigned char* s0 = buf + size_t(ti) * 128 * C::RB;
+    for (int i = lt; i < 128 * C::KB * 8; i += 128) {
+      const int row = i / (C::KB * 8), j = i % (C::KB * 8);
+      cp_async16(abase + (j >> 3) * 16384 + row * 128 + (((j & 7) ^ (row & 7)) << 4),
+                 s0 + size_t(row) * C::RB + j * 16);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+
   // One pass over all tiles of this warpgroup.  Returns false (uniformly over
   // the warpgroup) if an MMA wait expired; the expired phase stays pending.
-  static __device__ bool run(int pass, int wg, int lt, unsigned char* atile, uint32_t abase, uint32_t bbase,
+  template <int pass>
+  static __device__ __forceinline__ bool run(int wg, int lt, unsigned char* atile, uint32_t abase, uint32_t bbase,
                              uint32_t tacc, uint32_t tG,
                              uint32_t& phase, bool& pending, MixShared& sh, const Tio* __restrict__ f, Tio* __restrict__ Q,
                              float2* Fs, unsigned char* buf,
                              const float2* __restrict__ tab_t, float in_scale, float out_scale, bool first_term,
                              bool last_term, bool& bad, float& lmax) {
-    const int rows = (pass == kMF1 || pass == kMF0) ? H * N : N * N;
-    const int nout = pass == kMF2 ? N : C::NOUT;
+    constexpr int rows = (pass == kMF1 || pass == kMF0) ? H * N : N * N;
+    constexpr int nout = pass == kMF2 ? N : C::NOUT;
     const int q = lt >> 5;
     for (int ti = wg; ti < rows / 128; ti += kMixWG) {
       const int r = ti * 128 + lt;
       // ---- A tile
-      if (pass == kMF2) {
+      if constexpr (pass == kMF2) {
         const Tio* fr = f + size_t(r) * N;
 #pragma unroll 1
         for (int k0 = 0; k0 < N; k0 += 4) {
@@ -259,7 +270,7 @@ struct MixCell {
           *reinterpret_cast<uint4*>(atile + a_off(lt, 4 * k0)) = make_uint4(h[0], h[1], h[2], h[3]);
           *reinterpret_cast<uint4*>(atile + a_off(lt, 4 * N + 4 * k0)) = make_uint4(l[0], l[1], l[2], l[3]);
         }
-      } else if (pass == kMX) {
+      } else if constexpr (pass == kMX) {
         // Row (k0, k1): z[k2] = (A + iB) F for k2 < N/2 from row (k0, k1) of F
         // and of the term's table, for k2 > N/2 from the partner row (-k0, -k1)
         // at N - k2 (conjugated F).  Work item (row, j) covers k2 = 2j, 2j + 1
@@ -299,12 +310,7 @@ struct MixCell {
           *reinterpret_cast<uint32_t*>(atile + a_off(row, 4 * N + 4 * k2a)) = b0.y;
         }
       } else {
-        const unsigned char* s0 = buf + size_t(ti) * 128 * C::RB;
-        for (int i = lt; i < 128 * C::KB * 8; i += 128) {
-          const int row = i / (C::KB * 8), j = i % (C::KB * 8);
-          cp_async16(abase + (j >> 3) * 16384 + row * 128 + (((j & 7) ^ (row & 7)) << 4),
-                     s0 + size_t(row) * C::RB + j * 16);
-        }
+        if (ti == wg) load_tile(buf, ti, lt, abase);     // first tile; later ones were prefetched
         cp_async_wait_all();
       }
       fence_async_smem();
@@ -333,6 +339,9 @@ struct MixCell {
       }
       phase ^= 1u;
       fence_after();
+      // the MMAs have read the A tile: start copying this warpgroup's next tile
+      // of the pass so that the copy overlaps the epilogue
+      if (pass != kMF2 && pass != kMX && ti + kMixWG < rows / 128) load_tile(buf, ti + kMixWG, lt, abase);
       // ---- epilogue: thread = TMEM lane = pencil row r
       const uint32_t lane_base = static_cast<uint32_t>(32 * q) << 16;
       for (int c0 = 0; c0 < nout; c0 += 32) {
@@ -340,7 +349,7 @@ struct MixCell {
         tld32(tacc + lane_base + c0, a);
         const int v0c = c0 >> 1;                         // first output index of this chunk
         const int ne = (nout >> 1) - v0c < 16 ? (nout >> 1) - v0c : 16;
-        if (pass == kMZ) {
+        if constexpr (pass == kMZ) {
           // G[(v0, v1)][v2] for v2 = v0c .. v0c + 15
           const uint32_t gaddr = tG + lane_base + ti * N + v0c;
           uint32_t g[16];
@@ -364,7 +373,7 @@ struct MixCell {
               qr[size_t(e) * N * N] = Tio(gv);
             }
           }
-        } else if (pass == kMF0) {
+        } else if constexpr (pass == kMF0) {
           const int k2h = r / N, k1 = r % N;
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
@@ -376,25 +385,21 @@ struct MixCell {
             Fs[(size_t(k0) * N + k1) * H + k2h] = make_float2(re, im);
           }
         } else {
-          // split and store into the next pass's row, slot = this pencil's next-K index
-          int drow0, dstride, slot;
-          if (pass == kMF2) {          // r = (v0, v1), out k2h -> row (k2h, v0), slot v1
-            drow0 = r / N; dstride = N; slot = r % N;
-          } else if (pass == kMF1) {   // r = (k2h, v0), out k1 -> row (k2h, k1), slot v0
-            drow0 = (r / N) * N; dstride = 1; slot = r % N;
-          } else if (pass == kMX) {    // r = (k0, k1), out v2 -> row (v2, k0), slot k1
-            drow0 = r / N; dstride = N; slot = r % N;
-          } else {                     // kMY: r = (v2, k0), out v1 -> row (v2, v1), slot k0
-            drow0 = (r / N) * N; dstride = 1; slot = r % N;
-          }
+          // split and store into the next pass's row, slot = this pencil's next-K index:
+          //   F2: r = (v0, v1), out k2h -> row (k2h, v0), slot v1
+          //   F1: r = (k2h, v0), out k1 -> row (k2h, k1), slot v0
+          //   X:  r = (k0, k1), out v2 -> row (v2, k0), slot k1
+          //   Y:  r = (v2, k0), out v1 -> row (v2, v1), slot k0
+          constexpr int dstride = (pass == kMF2 || pass == kMX) ? N : 1;
+          const int drow0 = (pass == kMF2 || pass == kMX) ? r / N : (r / N) * N;
+          unsigned char* base0 = buf + size_t(drow0 + v0c * dstride) * C::RB + (r % N) * 4;
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             if (e >= ne) break;
-            const int v = v0c + e;
             const uint2 s = split2(__uint_as_float(a[2 * e]), __uint_as_float(a[2 * e + 1]));
-            unsigned char* rowp = buf + size_t(drow0 + v * dstride) * C::RB;
-            *reinterpret_cast<uint32_t*>(rowp + slot * 4) = s.x;
-            *reinterpret_cast<uint32_t*>(rowp + 4 * N + slot * 4) = s.y;
+            unsigned char* rowp = base0 + size_t(e) * dstride * C::RB;
+            *reinterpret_cast<uint32_t*>(rowp) = s.x;
+            *reinterpret_cast<uint32_t*>(rowp + 4 * N) = s.y;
           }
         }
       }
@@ -430,13 +435,13 @@ struct MixCell {
     __syncthreads();
     const int ef = cap - exp_of(sh.fmax);
     float lmax = 0.0f;
-    run(kMF2, wg, lt, atile, abase, bbase, tacc, tG, phase, pending, sh, f, Q, Fs, buf, tab, ldexpf(1.0f, ef), 1.0f,
+    run<kMF2>(wg, lt, atile, abase, bbase, tacc, tG, phase, pending, sh, f, Q, Fs, buf, tab, ldexpf(1.0f, ef), 1.0f,
         false, false, bad, lmax);
     if (stop()) return true;
-    run(kMF1, wg, lt, atile, abase, bbase, tacc, tG, phase, pending, sh, f, Q, Fs, buf, tab, 1.0f, 1.0f, false,
+    run<kMF1>(wg, lt, atile, abase, bbase, tacc, tG, phase, pending, sh, f, Q, Fs, buf, tab, 1.0f, 1.0f, false,
         false, bad, lmax);
     if (stop()) return true;
-    run(kMF0, wg, lt, atile, abase, bbase, tacc, tG, phase, pending, sh, f, Q, Fs, buf, tab, 1.0f, ldexpf(1.0f, -ef),
+    run<kMF0>(wg, lt, atile, abase, bbase, tacc, tG, phase, pending, sh, f, Q, Fs, buf, tab, 1.0f, ldexpf(1.0f, -ef),
         false, false, bad, lmax);
     atomic_max_nonneg(&sh.Fmax, lmax);
     if (stop()) return true;
@@ -445,13 +450,13 @@ struct MixCell {
       const float bound = __fmul_ru(__fmul_ru(Fmax, tmax[t]), 1.0000005f);
       const int et = cap - exp_of(bound);
       const float2* tab_t = tab + size_t(t) * N * N * H;
-      run(kMX, wg, lt, atile, abase, bbase, tacc, tG, phase, pending, sh, f, Q, Fs, buf, tab_t, ldexpf(1.0f, et),
+      run<kMX>(wg, lt, atile, abase, bbase, tacc, tG, phase, pending, sh, f, Q, Fs, buf, tab_t, ldexpf(1.0f, et),
           1.0f, false, false, bad, lmax);
       if (stop()) return true;
-      run(kMY, wg, lt, atile, abase, bbase, tacc, tG, phase, pending, sh, f, Q, Fs, buf, tab_t, 1.0f, 1.0f, false,
+      run<kMY>(wg, lt, atile, abase, bbase, tacc, tG, phase, pending, sh, f, Q, Fs, buf, tab_t, 1.0f, 1.0f, false,
           false, bad, lmax);
       if (stop()) return true;
-      run(kMZ, wg, lt, atile, abase, bbase, tacc, tG, phase, pending, sh, f, Q, Fs, buf, tab_t, 1.0f,
+      run<kMZ>(wg, lt, atile, abase, bbase, tacc, tG, phase, pending, sh, f, Q, Fs, buf, tab_t, 1.0f,
           ldexpf(1.0f, -2 * et), t == 0, t == n_terms - 1, bad, lmax);
       if (stop()) return true;
     }
