@@ -3,17 +3,22 @@
 Requests (cells x N^3, lambda, precision, a number of repeated evaluations)
 arrive over time.  Between GPU iterations the loop admits waiting requests in
 arrival order while they fit the HBM budget (f, Q and a share of the ragged
-workspace), keeps every admitted request's f resident on the device, and runs
-ONE ragged persistent launch per compute type over the cells of all active
-requests (coll_eval_ragged), followed by f <- f + dt Q (coll_advance).  A
-request leaves after its last evaluation; its memory returns to the budget and
-the next waiting requests join the following iteration.  Latency is measured
-from arrival to the completion of the request's last evaluation.
+workspace) and keeps every admitted request's f resident on the device.  Each
+iteration evaluates the active requests oldest first, up to a cost budget per
+iteration (at least one request), so that early requests finish early instead
+of every request advancing in lockstep: ONE ragged persistent launch per SIMT
+compute type over the cells of the selected requests (coll_eval_ragged), one
+tensor-core launch per selected mixed-precision request, then
+f <- f + dt Q (coll_advance).  A request leaves after its last evaluation; its
+memory returns to the budget and the next waiting requests are admitted.
+Latency is measured from arrival to the completion of the request's last
+evaluation.
 
-Precision classes: "f32" runs the FP32 kernels; "mixed" runs float-pair
-(f32x2) transforms where the kernel supports the grid (N <= 32) and FP32 above.
-Each cell's arithmetic does not depend on what else is in the batch, so a
-request's result is the same alone and in the mix (tests/test_gpu_service.py).
+Precision classes: "f32" runs the FP32 kernels; "mixed" runs the tensor-core
+DFT-GEMM path (f16 hi+lo, COLL_MIXED_F16X2) where it supports the grid
+(N = 16, 32) and FP32 above.  Each cell's arithmetic does not depend on what
+else is in the batch, so a request's result is the same alone and in the mix
+(tests/test_gpu_service.py).
 """
 from __future__ import annotations
 
@@ -27,13 +32,20 @@ import numpy as np
 
 from . import coll, synth
 
-KIND = {"f32": "f32", "mixed": "f32x2"}
-
-
 def effective_precision(precision: str, N: int) -> str:
     if precision == "mixed":
-        return "f32x2" if N <= 32 else "f32"
+        return "mixed_f16x2" if N in (16, 32) else "f32"
     return precision
+
+
+# relative GPU time per cell-evaluation by compute type (measured at N = 32, 25 terms)
+SPEED = {"f32": 1.0, "mixed_f16x2": 0.83, "f32x2": 7.6, "f64": 23.0}
+
+
+def cell_cost(N: int, lam: float, prec: str, M: int = 48, Mr: int = 8) -> float:
+    """Relative cost of one cell-evaluation: terms x N^3 log2 N^3 x the compute type's speed."""
+    terms = M // 2 + 1 if lam == 1.0 else (M // 2) * Mr + 1
+    return terms * N ** 3 * math.log2(N ** 3) * SPEED.get(prec, 1.0)
 
 
 @dataclasses.dataclass
@@ -59,7 +71,7 @@ class Job:
 
 class Service:
     def __init__(self, hbm_budget_bytes: float = 120e9, L: float = synth.DEFAULT_L, M: int = 48, Mtheta: int = 4,
-                 device: str = "cuda"):
+                 device: str = "cuda", iter_budget_cells: float = 2048.0):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -71,14 +83,18 @@ class Service:
         self.in_use = 0
         self.peak_in_use = 0
         self.stats = collections.Counter()
+        # cost budget of one iteration, in N = 32, lambda = 1, FP32 cell-evaluations
+        self.iter_budget = iter_budget_cells * cell_cost(32, 1.0, "f32", M=M)
+        self.min_cells = 2 * torch.cuda.get_device_properties(self.device).multi_processor_count
 
     # ---------------------------------------------------------------- plans
     def plan(self, N: int, lam: float, prec: str):
         key = (N, float(lam), prec)
         if key not in self.plans:
             Mr = 16 if lam == 1.0 else 8
+            io = 1 if prec in ("f32", "mixed_f16x2") else 0
             self.plans[key] = coll.Plan(N, self.L, lam=lam, M=self.M, Mtheta=self.Mtheta, Mr=Mr, prec=prec,
-                                        max_cells=1, device=self.device)
+                                        io_dtype=io, max_cells=1, device=self.device)
         return self.plans[key]
 
     def warm_plans(self, Ns=(16, 32, 48, 64), lams=(0.0, 1.0), precisions=("f32", "mixed")):
@@ -90,7 +106,7 @@ class Service:
     # -------------------------------------------------------------- memory
     def _job_bytes(self, j: Job) -> int:
         prec = effective_precision(j.precision, j.N)
-        es = 8 if prec == "f32x2" else 4
+        es = 8 if prec in ("f32x2", "f64") else 4
         return 2 * j.n_cells * j.N ** 3 * es
 
     def _ensure_ws(self, nbytes: int):
@@ -100,7 +116,7 @@ class Service:
     def _admit(self, j: Job, now: float):
         torch = self.torch
         prec = effective_precision(j.precision, j.N)
-        dt = torch.float64 if prec == "f32x2" else torch.float32
+        dt = torch.float64 if prec in ("f32x2", "f64") else torch.float32
         with torch.cuda.stream(self.stream):
             if j.f_host is not None:
                 src = torch.as_tensor(j.f_host)
@@ -114,12 +130,34 @@ class Service:
         j.t_admit = now
 
     # ------------------------------------------------------------ one step
+    def _select(self, active):
+        """Oldest requests first, up to the iteration's cost budget, but with at
+        least two cells per SM (so that one heavy request does not leave most of
+        the GPU idle) and at least one request."""
+        chosen, cost, cells = [], 0.0, 0
+        for j in sorted(active, key=lambda j: (j.arrival_s, j.rid)):
+            c = j.n_cells * cell_cost(j.N, j.lam, effective_precision(j.precision, j.N), M=self.M)
+            if chosen and cost + c > self.iter_budget and cells >= self.min_cells:
+                continue
+            chosen.append(j)
+            cost += c
+            cells += j.n_cells
+        return chosen
+
     def _iterate(self, active):
-        """One evaluation of every active job: ragged launch per compute type, then f += dt Q."""
+        """One evaluation of the selected jobs: ragged launch per SIMT compute type,
+        one tensor-core launch per mixed job, then f += dt Q."""
+        chosen = self._select(active)
         by_kind = collections.defaultdict(list)
-        for j in active:
+        for j in chosen:
             by_kind[effective_precision(j.precision, j.N)].append(j)
         for prec, jobs in by_kind.items():
+            if prec == "mixed_f16x2":
+                for j in jobs:
+                    p = self.plan(j.N, j.lam, prec)
+                    coll.coll_eval_batch(p.handle, j.f, j.Q, j.n_cells, p.reserve(j.n_cells), stream=self.stream)
+                    self.stats["launches"] += 1
+                continue
             for s in range(0, len(jobs), 256):
                 chunk = jobs[s:s + 256]
                 groups = [(self.plan(j.N, j.lam, prec).handle, j.f, j.Q) for j in chunk]
@@ -127,11 +165,11 @@ class Service:
                 self._ensure_ws(coll.coll_ragged_workspace_size(groups, cells))
                 coll.coll_eval_ragged(groups, cells, self.ws, stream=self.stream)
                 self.stats["launches"] += 1
-        for j in active:
+        for j in chosen:
             if j.done + 1 < j.n_evals:
                 coll.coll_advance(j.f, j.Q, j.dt, stream=self.stream)
         self.stream.synchronize()
-        for j in active:
+        for j in chosen:
             j.done += 1
             self.stats["cell_evals"] += j.n_cells
 
