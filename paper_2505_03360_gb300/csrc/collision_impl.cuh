@@ -121,6 +121,20 @@ __device__ __noinline__ bool run_pass(int mode, typename C2<T>::type* base, int 
   return bad;
 }
 
+// (xr, xi) times i^m, m in 0..3, by selects (the slab index is a runtime
+// value, so these exact rotations would otherwise cost a complex multiply).
+// Used for FP64, whose pipe bounds the kernel; for the FP32-pipe types the
+// extra branches and selects cost more than the multiplies they save.
+template <typename T> constexpr bool kQuarterBySelect = false;
+template <> constexpr bool kQuarterBySelect<double> = true;
+template <typename T>
+__device__ __forceinline__ void rotate_quarter(T& xr, T& xi, int m) {
+  const T r = xr, i = xi;
+  const T nr = -r, ni = -i;
+  xr = m == 0 ? r : (m == 1 ? ni : (m == 2 ? nr : i));
+  xi = m == 0 ? i : (m == 1 ? r : (m == 2 ? ni : nr));
+}
+
 // P1: axis-0 inverse of (A + iB) F for every full-spectrum pencil (k1, k2),
 // forming only the outputs v0 = s + S0 m (decimation in frequency):
 //   y[k'] = w_N^{s k'} sum_q x[k' + q NS] e^{2 pi i s q / S0},  then an NS-point IFFT.
@@ -155,20 +169,28 @@ __device__ __noinline__ void run_p1(const typename C2<T>::type* __restrict__ tb,
           T xi = AB.x * fi + AB.y * fr;
           if (S0 > 1 && q > 0) {
             const int n = (s * q * (192 / S0)) % 192;
-            const T c = Tw<T>::c(n), sn = Tw<T>::s(n);
-            const T rr = xr * c - xi * sn;
-            xi = xr * sn + xi * c;
-            xr = rr;
+            if (kQuarterBySelect<T> && n % 48 == 0) {
+              rotate_quarter(xr, xi, n / 48);             // +-1, +-i: no multiplies (uniform branch)
+            } else {
+              const T c = Tw<T>::c(n), sn = Tw<T>::s(n);
+              const T rr = xr * c - xi * sn;
+              xi = xr * sn + xi * c;
+              xr = rr;
+            }
           }
           ar = ar + xr;
           ai = ai + xi;
         }
         if (S0 > 1) {
           const int n = (s * kp * (192 / N)) % 192;
-          const T c = Tw<T>::c(n), sn = Tw<T>::s(n);
-          const T rr = ar * c - ai * sn;
-          ai = ar * sn + ai * c;
-          ar = rr;
+          if (kQuarterBySelect<T> && n % 48 == 0) {
+            rotate_quarter(ar, ai, n / 48);
+          } else {
+            const T c = Tw<T>::c(n), sn = Tw<T>::s(n);
+            const T rr = ar * c - ai * sn;
+            ai = ar * sn + ai * c;
+            ar = rr;
+          }
         }
         yr[kp] = ar;
         yi[kp] = ai;
