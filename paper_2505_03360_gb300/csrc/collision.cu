@@ -23,6 +23,7 @@ template <int N, typename T, int V> LayoutInfo make_info_v() {
   i.w_bytes = Ly::round16(Ly::W_BYTES);
   i.fh_bytes = Ly::round16(Ly::FH_BYTES);
   i.g_bytes = Ly::round16(Ly::G_BYTES);
+  i.extra_ws = Ly::round16(Ly::WG_BYTES) + Ly::round16(Ly::GG_BYTES);
   return i;
 }
 

@@ -202,6 +202,49 @@ __device__ __noinline__ void run_p1(const typename C2<T>::type* __restrict__ tb,
   }
 }
 
+// P1F: full axis-0 inverse of (A + iB) F for every full-spectrum pencil
+// (k1, k2) (no slab split), into the term buffer Wg[v0][k1][k2] (global).
+template <int N, typename T, int V>
+__device__ __noinline__ void run_p1f(const typename C2<T>::type* __restrict__ tb, const typename C2<T>::type* Fh,
+                                     typename C2<T>::type* Wg) {
+  using Ly = Lay<N, T, V>;
+  using V2 = typename C2<T>::type;
+  constexpr int H = Ly::H, FR = Ly::FH_ROW;
+  for (int pid = threadIdx.x; pid < N * N; pid += kThreads) {
+    const int k1 = pid / N, k2 = pid % N;
+    T xr[N], xi[N];
+    if (k2 == H || k1 == H) {
+#pragma unroll
+      for (int k0 = 0; k0 < N; ++k0) { xr[k0] = T{}; xi[k0] = T{}; }
+    } else {
+      const bool up = k2 > H;
+      const int k2s = up ? N - k2 : k2;
+      const int k1s = up ? (N - k1) % N : k1;
+#pragma unroll
+      for (int k0 = 0; k0 < N; ++k0) {
+        const int k0s = up ? (N - k0) % N : k0;
+        const size_t idx = (size_t(k0s) * N + k1s);
+        const V2 F = Fh[idx * FR + k2s];
+        const V2 AB = tb[idx * H + k2s];
+        const T fr = F.x, fi = up ? -F.y : F.y;   // conj for the Hermitian partner
+        xr[k0] = AB.x * fr - AB.y * fi;
+        xi[k0] = AB.x * fi + AB.y * fr;
+      }
+      fft<N, +1, T>(xr, xi);
+    }
+#pragma unroll
+    for (int v0 = 0; v0 < N; ++v0) Wg[(size_t(v0) * N + k1) * N + k2] = V2{xr[v0], xi[v0]};
+  }
+}
+
+// 16-byte asynchronous global -> shared copies (and their completion)
+__device__ __forceinline__ void cp16(void* dst_smem, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(dst_smem))),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp16_wait() { asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory"); }
+
 // ------------------------------------------------------------ per-cell body
 // smem: dynamic shared memory base; wsc: this CTA's workspace slice.
 template <int N, typename T, typename Tio, int V = 0>
@@ -228,6 +271,50 @@ __device__ __forceinline__ void process_cell(const Tio* __restrict__ f, Tio* __r
   __syncthreads();
   run_pass<N, T, Tio>(kPassFwd, Fh, N * H, H, FR, 1, N * FR, -1, f, Q, G, 0, S0, FR, false);
   __syncthreads();
+
+  if constexpr (Cf::P1F) {
+    // terms outer: one full axis-0 pass per term into Wg, then per slab (planes
+    // v0 = s NS .. s NS + NS - 1): copy the slab into W, restore the slab's
+    // gain accumulator, axis 1, axis 2 with G += Re*Im (Q on the last term),
+    // save the accumulator.
+    V2* Wg = reinterpret_cast<V2*>(gp);
+    gp += Ly::round16(Ly::WG_BYTES);
+    T* Gg = reinterpret_cast<T*>(gp);
+    constexpr int GSLAB = NS * N * (N + 1);                 // doubles of one slab of G
+    for (int t = 0; t < n_terms; ++t) {
+      run_p1f<N, T, V>(tab + size_t(t) * N * N * H, Fh, Wg);
+      __syncthreads();
+      for (int s = 0; s < S0; ++s) {
+        const V2* src = Wg + size_t(s) * NS * N * N;
+        for (int i = threadIdx.x; i < NS * N * N; i += kThreads) {
+          const int m = i / (N * N), rem = i % (N * N);
+          cp16(W + (size_t(m) * N + rem / N) * WR + rem % N, src + i);
+        }
+        if (t == 0) {
+          for (int i = threadIdx.x; i < GSLAB; i += kThreads) G[i] = T{};
+        } else {
+          static_assert((GSLAB * sizeof(T)) % 16 == 0, "G slab copy in 16-byte pieces");
+          const unsigned char* gsrc = reinterpret_cast<const unsigned char*>(Gg + size_t(s) * GSLAB);
+          for (int i = threadIdx.x; i < GSLAB * int(sizeof(T)) / 16; i += kThreads)
+            cp16(reinterpret_cast<unsigned char*>(G) + 16 * i, gsrc + 16 * i);
+        }
+        cp16_wait();
+        __syncthreads();
+        run_pass<N, T, Tio>(kPassInv, W, NS * N, N, N * WR, 1, WR, H, f, Q, G, s * NS, 1, FR, false);
+        __syncthreads();
+        const bool last = t == n_terms - 1;
+        bad |= run_pass<N, T, Tio>(kPassP3, W, NS * N, N, N * WR, WR, 1, -1, f, Q, G, s * NS, 1, FR, last);
+        __syncthreads();
+        if (!last) {
+          uint4* gdst = reinterpret_cast<uint4*>(Gg + size_t(s) * GSLAB);
+          const uint4* gs = reinterpret_cast<const uint4*>(G);
+          for (int i = threadIdx.x; i < GSLAB * int(sizeof(T)) / 16; i += kThreads) gdst[i] = gs[i];
+          __syncthreads();
+        }
+      }
+    }
+    return;
+  }
 
   for (int s = 0; s < S0; ++s) {
     for (int i = threadIdx.x; i < NS * N * (N + 1); i += kThreads) G[i] = T{};

@@ -17,16 +17,28 @@ template <> struct C2<df> { using type = cdf; };
 // memory (W = one slab of the per-term spectrum, Fh = forward half spectrum,
 // G = one slab of the gain accumulator); whether Fh rows are padded.  Two
 // variants per (N, type) give the autotuner two slab shapes to choose from.
+// P1F (full first pass): the axis-0 inverse of each term runs once over full
+// pencils into a global buffer of the whole term, and the slabs are copied
+// from it (terms outer, slabs inner, the gain accumulator of each slab saved
+// to and restored from global memory); otherwise (terms inner, slabs outer)
+// every slab re-forms its planes from the spectrum by decimation in frequency.
 template <int N, typename T, int V = 0> struct Cfg;
 #define COLL_CFG(N_, T_, V_, S0_, W_, FH_, G_, PAD_)                                      \
   template <> struct Cfg<N_, T_, V_> {                                                     \
     static constexpr int S0 = S0_;                                                         \
     static constexpr bool W = W_, FH = FH_, G = G_, FH_PAD = PAD_;                         \
+    static constexpr bool P1F = false;                                                     \
+  };
+#define COLL_CFG_P1F(N_, T_, V_, S0_, FH_, PAD_)                                           \
+  template <> struct Cfg<N_, T_, V_> {                                                     \
+    static constexpr int S0 = S0_;                                                         \
+    static constexpr bool W = true, FH = FH_, G = true, FH_PAD = PAD_;                     \
+    static constexpr bool P1F = true;                                                      \
   };
 //        N   T      V  S0  W     Fh     G      Fh padded
 COLL_CFG(16, double, 0,  1, true, true,  true,  true)
 COLL_CFG(24, double, 0,  2, true, false, true,  true)
-COLL_CFG(32, double, 0,  4, true, false, true,  true)
+COLL_CFG_P1F(32, double, 0, 4, false, true)
 COLL_CFG(16, df,     0,  1, true, true,  true,  true)
 COLL_CFG(24, df,     0,  2, true, false, true,  true)
 COLL_CFG(32, df,     0,  4, true, false, true,  true)
@@ -47,6 +59,7 @@ COLL_CFG(32, float,  1,  2, true, false, true,  true)
 COLL_CFG(48, float,  1,  4, true, false, false, true)
 COLL_CFG(64, float,  1,  8, false, false, true, true)
 #undef COLL_CFG
+#undef COLL_CFG_P1F
 
 constexpr int kThreads = 256;
 
@@ -64,8 +77,11 @@ template <int N, typename T, int V = 0> struct Lay {
   static constexpr size_t round16(size_t b) { return (b + 15) / 16 * 16; }
   static constexpr size_t SMEM = (Cf::W ? round16(W_BYTES) : 0) + (Cf::FH ? round16(FH_BYTES) : 0) +
                                  (Cf::G ? round16(G_BYTES) : 0);
+  // P1F: the whole term's spectrum after the axis-0 pass and the whole gain accumulator
+  static constexpr size_t WG_BYTES = Cf::P1F ? size_t(N) * N * N * 2 * sizeof(T) : 0;
+  static constexpr size_t GG_BYTES = Cf::P1F ? size_t(N) * N * G_ROW * sizeof(T) : 0;
   static constexpr size_t WS = (Cf::W ? 0 : round16(W_BYTES)) + (Cf::FH ? 0 : round16(FH_BYTES)) +
-                               (Cf::G ? 0 : round16(G_BYTES));
+                               (Cf::G ? 0 : round16(G_BYTES)) + round16(WG_BYTES) + round16(GG_BYTES);
   static_assert(SMEM <= 232448, "shared-memory layout exceeds 227 KB");
   static_assert(N % S0 == 0, "S0 must divide N");
 };
