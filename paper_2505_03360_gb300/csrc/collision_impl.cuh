@@ -237,11 +237,21 @@ __device__ __noinline__ void run_p1f(const typename C2<T>::type* __restrict__ tb
   }
 }
 
-// 16-byte asynchronous global -> shared copies (and their completion)
+// asynchronous global -> shared copies of 16 or 8 bytes (and their completion);
+// both addresses aligned to the copy size
 __device__ __forceinline__ void cp16(void* dst_smem, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(dst_smem))),
                "l"(src)
                : "memory");
+}
+__device__ __forceinline__ void cp8(void* dst_smem, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(dst_smem))),
+               "l"(src)
+               : "memory");
+}
+template <typename V2> __device__ __forceinline__ void cp_elem(V2* dst_smem, const V2* src) {
+  static_assert(sizeof(V2) == 16 || sizeof(V2) == 8, "complex element of 8 or 16 bytes");
+  if constexpr (sizeof(V2) == 16) cp16(dst_smem, src); else cp8(dst_smem, src);
 }
 __device__ __forceinline__ void cp16_wait() { asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory"); }
 
@@ -288,7 +298,7 @@ __device__ __forceinline__ void process_cell(const Tio* __restrict__ f, Tio* __r
         const V2* src = Wg + size_t(s) * NS * N * N;
         for (int i = threadIdx.x; i < NS * N * N; i += kThreads) {
           const int m = i / (N * N), rem = i % (N * N);
-          cp16(W + (size_t(m) * N + rem / N) * WR + rem % N, src + i);
+          cp_elem(W + (size_t(m) * N + rem / N) * WR + rem % N, src + i);
         }
         if (t == 0) {
           for (int i = threadIdx.x; i < GSLAB; i += kThreads) G[i] = T{};

@@ -37,14 +37,14 @@ template <int N, typename T, int V = 0> struct Cfg;
   };
 //        N   T      V  S0  W     Fh     G      Fh padded
 COLL_CFG(16, double, 0,  1, true, true,  true,  true)
-COLL_CFG(24, double, 0,  2, true, false, true,  true)
+COLL_CFG_P1F(24, double, 0, 2, false, true)
 COLL_CFG_P1F(32, double, 0, 4, false, true)
 COLL_CFG(16, df,     0,  1, true, true,  true,  true)
 COLL_CFG(24, df,     0,  2, true, false, true,  true)
 COLL_CFG(32, df,     0,  4, true, false, true,  true)
 COLL_CFG(16, float,  0,  1, true, true,  true,  true)
 COLL_CFG(24, float,  0,  1, true, true,  true,  false)
-COLL_CFG(32, float,  0,  4, true, true,  true,  false)
+COLL_CFG_P1F(32, float,  0, 4, true, false)
 COLL_CFG(48, float,  0,  8, true, false, true,  true)
 COLL_CFG(64, float,  0, 16, true, false, true,  true)
 COLL_CFG(16, double, 1,  2, true, true,  true,  true)
