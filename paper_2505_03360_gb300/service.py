@@ -32,6 +32,13 @@ import numpy as np
 
 from . import coll, synth
 
+
+def torch_event(stream):
+    import torch
+    e = torch.cuda.Event()
+    e.record(stream)
+    return e
+
 def effective_precision(precision: str, N: int) -> str:
     if precision == "mixed":
         return "mixed_f16x2" if N in (16, 32) else "f32"
@@ -79,6 +86,8 @@ class Service:
         self.L, self.M, self.Mtheta = L, M, Mtheta
         self.plans = {}
         self.stream = torch.cuda.Stream(device=self.device)
+        # tensor-core launches (one per mixed request, few CTAs each) run concurrently on side streams
+        self.side = [torch.cuda.Stream(device=self.device) for _ in range(8)]
         self.ws = None
         self.in_use = 0
         self.peak_in_use = 0
@@ -95,6 +104,15 @@ class Service:
             io = 1 if prec in ("f32", "mixed_f16x2") else 0
             self.plans[key] = coll.Plan(N, self.L, lam=lam, M=self.M, Mtheta=self.Mtheta, Mr=Mr, prec=prec,
                                         io_dtype=io, max_cells=1, device=self.device)
+        return self.plans[key]
+
+    def _mix_plan(self, j, lane):
+        """Tensor-core plan for job j on side stream `lane` (each lane owns its workspace)."""
+        key = (j.N, float(j.lam), "mixed_f16x2", lane)
+        if key not in self.plans:
+            Mr = 16 if j.lam == 1.0 else 8
+            self.plans[key] = coll.Plan(j.N, self.L, lam=j.lam, M=self.M, Mtheta=self.Mtheta, Mr=Mr,
+                                        prec="mixed_f16x2", io_dtype=1, max_cells=1, device=self.device)
         return self.plans[key]
 
     def warm_plans(self, Ns=(16, 32, 48, 64), lams=(0.0, 1.0), precisions=("f32", "mixed")):
@@ -151,12 +169,18 @@ class Service:
         by_kind = collections.defaultdict(list)
         for j in chosen:
             by_kind[effective_precision(j.precision, j.N)].append(j)
+        side_used = []
         for prec, jobs in by_kind.items():
             if prec == "mixed_f16x2":
-                for j in jobs:
-                    p = self.plan(j.N, j.lam, prec)
-                    coll.coll_eval_batch(p.handle, j.f, j.Q, j.n_cells, p.reserve(j.n_cells), stream=self.stream)
+                ready = torch_event(self.stream)
+                for i, j in enumerate(jobs):
+                    st = self.side[i % len(self.side)]
+                    st.wait_event(ready)
+                    p = self._mix_plan(j, i % len(self.side))
+                    coll.coll_eval_batch(p.handle, j.f, j.Q, j.n_cells, p.reserve(j.n_cells), stream=st)
                     self.stats["launches"] += 1
+                    if st not in side_used:
+                        side_used.append(st)
                 continue
             for s in range(0, len(jobs), 256):
                 chunk = jobs[s:s + 256]
@@ -165,6 +189,8 @@ class Service:
                 self._ensure_ws(coll.coll_ragged_workspace_size(groups, cells))
                 coll.coll_eval_ragged(groups, cells, self.ws, stream=self.stream)
                 self.stats["launches"] += 1
+        for st in side_used:
+            self.stream.wait_event(torch_event(st))
         for j in chosen:
             if j.done + 1 < j.n_evals:
                 coll.coll_advance(j.f, j.Q, j.dt, stream=self.stream)
