@@ -1,5 +1,5 @@
 /*
- * coll_debug.h -- host-only inspection entry point of libcoll.so.
+ * coll_debug.h -- inspection and failure-injection entry points of libcoll.so.
  *
  * coll_plan_tables_host builds, on the host and without touching any GPU, the
  * multiplier tables a plan would upload (sec. 4.4.1, separated kernel
@@ -22,6 +22,19 @@ extern "C" {
 
 coll_status coll_plan_tables_host(const coll_plan_desc* desc, double* out, size_t cap, int32_t* n_terms,
                                   size_t* n_doubles);
+
+/*
+ * coll_debug_mixed_drop_commit -- failure injection for the bounded waits of
+ * the tensor-core path (COLL_MIXED_F16X2).  With on != 0, in every later
+ * launch warpgroup 0 of each CTA omits the completion signal of its first MMA
+ * batch: its wait expires after about one second of SM clocks, the CTA stops,
+ * waits (bounded) once more, frees its tensor memory and returns, and the
+ * plan's sticky status reads COLL_ETIMEOUT (coll_device_status).  Nothing
+ * faults or hangs; the launch takes about two seconds.  on = 0 restores normal
+ * operation.  Applies to the current device.  Returns COLL_ECUDA if the switch
+ * cannot be written.
+ */
+coll_status coll_debug_mixed_drop_commit(int32_t on);
 
 #ifdef __cplusplus
 }

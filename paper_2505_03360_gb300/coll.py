@@ -70,6 +70,7 @@ def _load():
         "coll_launch_count": (I64, []),
         "coll_plan_tables_host": (I32, [ctypes.POINTER(coll_plan_desc), P, SZ, ctypes.POINTER(I32),
                                         ctypes.POINTER(SZ)]),
+        "coll_debug_mixed_drop_commit": (I32, [I32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -88,6 +89,11 @@ def header_functions() -> list:
         txt = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
         names.update(re.findall(r"^[A-Za-z_][\w\s\*]*?\b(coll_\w+|moments_realizability)\s*\(", txt, re.M))
     return sorted(names)
+
+
+def coll_debug_mixed_drop_commit(on: bool):
+    """Failure injection for the tensor-core path's bounded waits (see coll_debug.h)."""
+    _check(_lib.coll_debug_mixed_drop_commit(1 if on else 0), "coll_debug_mixed_drop_commit")
 
 
 def coll_status_string(status: int) -> str:

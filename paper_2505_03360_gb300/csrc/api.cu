@@ -237,6 +237,10 @@ coll_status coll_plan_tables_host(const coll_plan_desc* desc, double* out, size_
   return COLL_OK;
 }
 
+coll_status coll_debug_mixed_drop_commit(int32_t on) {
+  return mixed_set_drop_commit(on) == 0 ? COLL_OK : COLL_ECUDA;
+}
+
 coll_status coll_plan_destroy(coll_plan p) {
   if (!p) return COLL_EINVAL;
   cudaFree(p->tab_dev);

@@ -104,6 +104,7 @@ int ragged_max_ctas_per_sm(int ctype, int* ctas);
 bool mixed_layout(int N, LayoutInfo* out);
 int launch_mixed(int N, bool io_f64, const CollArgs& a, int grid, void* stream);
 int mixed_max_ctas_per_sm(int N, bool io_f64, int* ctas);
+int mixed_set_drop_commit(int on);      // failure injection (coll_debug.h)
 
 // Moments kernel (moments.cu)
 int launch_moments(const void* f, int io_f64, int N, double L, long long n_cells, double eta0,

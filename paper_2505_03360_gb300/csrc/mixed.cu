@@ -216,10 +216,16 @@ __device__ __forceinline__ void atomic_max_nonneg(float* a, float v) {
 
 enum MixPass : int { kMF2 = 0, kMF1, kMF0, kMX, kMY, kMZ };
 
+// Failure-injection switch for the bounded-wait test (coll_debug_mixed_drop_commit):
+// when set, warpgroup 0 of every CTA omits the completion signal of its first
+// MMA batch, so that its wait expires.
+__device__ int g_mix_drop_commit = 0;
+
 struct MixShared {
   uint64_t bar[kMixWG];
   uint32_t tbase;
   int abort;
+  int drop_commit;
   int bad;
   float fmax;
   float Fmax;
@@ -330,7 +336,8 @@ struct MixCell {
         for (int kk = 0; kk < 2 * N / 16; ++kk)           // B2 over the hi parts: X_h D_l
           mma_f16(tacc, sw128_desc(abase + (kk >> 2) * 16384 + (kk & 3) * 32),
                   sw128_desc(bbase + C::B1_SET + (kk >> 2) * (C::NOUT * 128) + (kk & 3) * 32), id, 1u);
-        mma_commit(&sh.bar[wg]);
+        if (wg == 0 && sh.drop_commit) sh.drop_commit = 0;   // injected failure: no completion signal
+        else mma_commit(&sh.bar[wg]);
       }
       if (!wg_all(wg, wait_parity(&sh.bar[wg], phase))) {
         if (lt == 0) atomicExch(&sh.abort, 1);
@@ -490,6 +497,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) mixed_kernel(CollArgs a) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&sh.bar[w])), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     sh.abort = 0;
+    sh.drop_commit = g_mix_drop_commit;
   }
   fence_async_smem();
   fence_before();
@@ -555,6 +563,11 @@ double half_value(uint16_t b) {
 }
 
 }  // namespace
+
+int mixed_set_drop_commit(int on) {
+  const int v = on ? 1 : 0;
+  return int(cudaMemcpyToSymbol(g_mix_drop_commit, &v, sizeof(int)));
+}
 
 bool mixed_layout(int N, LayoutInfo* out) {
   if (N != 16 && N != 32) return false;

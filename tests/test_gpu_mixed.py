@@ -103,3 +103,32 @@ def test_mixed_unsupported_shapes():
         coll.coll_ragged_workspace_size([(p.handle, f, torch.empty_like(f))], [1])
     assert e.value.status == coll.COLL_EUNSUPPORTED
     p.close()
+
+
+def test_bounded_wait_expires_and_reports_timeout():
+    """Failure injection: warpgroup 0's first MMA batch never signals completion.
+    The launch returns after its bounded waits (about two seconds), the plan's
+    sticky status reads COLL_ETIMEOUT, the context stays usable, and with the
+    injection off the same plan evaluates correctly again."""
+    import time
+    N = 16
+    p = coll.Plan(N, L, lam=1.0, M=32, Mtheta=4, Mr=8, prec="mixed_f16x2", max_cells=1)
+    f = torch.from_numpy(synth.bimodal_batch(1, N, L, seed=9)).cuda()
+    ref = p.eval(f).clone()
+    torch.cuda.synchronize()
+    try:
+        coll.coll_debug_mixed_drop_commit(True)
+        t0 = time.perf_counter()
+        p.eval(f)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    finally:
+        coll.coll_debug_mixed_drop_commit(False)
+    assert p.status() == coll.COLL_ETIMEOUT
+    assert 0.5 < dt < 30.0, dt
+    coll.coll_device_status_clear(p.handle)
+    Q = p.eval(f)
+    torch.cuda.synchronize()
+    assert p.status() == coll.COLL_OK
+    assert torch.equal(Q, ref)
+    p.close()
