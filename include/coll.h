@@ -57,8 +57,11 @@ typedef enum {
 typedef enum {
   COLL_F64 = 0,           /* transforms and products in FP64                  */
   COLL_F32 = 1,           /* transforms and products in FP32                  */
-  COLL_MIXED_F16X2 = 2,   /* DFT-GEMM on tensor cores, f16 hi+lo split        */
-  COLL_MIXED_BF16X3 = 3,  /* DFT-GEMM on tensor cores, bf16 three-term split  */
+  COLL_MIXED_F16X2 = 2,   /* every transform a DFT-GEMM on the tensor cores,
+                             f16 hi+lo operands (3 products), FP32 accumulate;
+                             N = 16, 32; not in ragged launches              */
+  COLL_MIXED_BF16X3 = 3,  /* the same with bf16 hi+mid+lo operands (6
+                             products); N = 16, 32; not in ragged launches   */
   COLL_F32X2 = 4          /* transforms in float pairs (hi + lo, ~48 bits) on
                              the FP32 pipe; N = 16, 24, 32                    */
 } coll_precision;
@@ -67,7 +70,7 @@ typedef enum {
  * Plan descriptor (sec. 4.4.1 "The 3d case", with the readings listed in the
  * design notes):
  *   N        points per velocity axis; 16, 24, 32, 48 or 64 (FP64 and
- *            COLL_F32X2: 16, 24, 32)
+ *            COLL_F32X2: 16, 24, 32; tensor-core precisions: 16, 32)
  *   L        half-width of the periodic velocity box [-L, L)^3
  *   S        support radius; truncation R = 2S (sec. 4.4.1, Q^R);
  *            0 selects S = 2L / (3 + sqrt 2), the no-overlap bound

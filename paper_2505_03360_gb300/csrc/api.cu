@@ -22,7 +22,7 @@ using namespace coll;
 namespace {
 
 bool valid_N(int N, int ctype) {
-  if (ctype == kCMixF16) return N == 16 || N == 32;
+  if (is_mixed(ctype)) return N == 16 || N == 32;
   if (ctype != kCF32) return N == 16 || N == 24 || N == 32;
   return N == 16 || N == 24 || N == 32 || N == 48 || N == 64;
 }
@@ -56,7 +56,7 @@ coll_status ragged_prepare(const coll_cell_group* groups, const int64_t* cells, 
   const coll_plan_s* p0 = groups[0].plan;
   if (!p0) return COLL_EINVAL;
   *ctype = p0->ctype;
-  if (p0->ctype == kCMixF16) return COLL_EUNSUPPORTED;     // the ragged kernel runs SIMT compute types only
+  if (is_mixed(p0->ctype)) return COLL_EUNSUPPORTED;      // the ragged kernel runs SIMT compute types only
   const bool want_io_f64 = p0->ctype != kCF32;
   int order[kMaxRaggedGroups];
   for (int i = 0; i < n; ++i) {
@@ -152,10 +152,10 @@ coll_status coll_plan_create(const coll_plan_desc* desc, coll_plan* out) {
       d.prec != COLL_F32X2)
     return COLL_EINVAL;
   if (d.dealias) return COLL_EUNSUPPORTED;
-  if (d.prec == COLL_MIXED_BF16X3) return COLL_EUNSUPPORTED;
   const int ctype = d.prec == COLL_F64 ? kCF64
                   : d.prec == COLL_F32 ? kCF32
-                  : d.prec == COLL_MIXED_F16X2 ? kCMixF16 : kCDF;
+                  : d.prec == COLL_MIXED_F16X2 ? kCMixF16
+                  : d.prec == COLL_MIXED_BF16X3 ? kCMixBF16 : kCDF;
   if (!valid_N(d.N, ctype)) return COLL_EUNSUPPORTED;
 
   HostTables ht;
@@ -183,8 +183,8 @@ coll_status coll_plan_create(const coll_plan_desc* desc, coll_plan* out) {
 
   const size_t n = ht.tab.size();
   std::vector<unsigned char> mix;
-  if (ctype == kCMixF16) {
-    st = build_mixed_image(ht, d.N, &mix);
+  if (is_mixed(ctype)) {
+    st = build_mixed_image(ht, d.N, mixed_parts(ctype), &mix);
     if (st != COLL_OK) { delete p; return st; }
     p->tab_bytes = mix.size();
   } else {
@@ -192,7 +192,7 @@ coll_status coll_plan_create(const coll_plan_desc* desc, coll_plan* out) {
   }
   if (cudaMalloc(&p->tab_dev, p->tab_bytes) != cudaSuccess) { delete p; return COLL_ENOMEM; }
   cudaError_t e;
-  if (ctype == kCMixF16) {
+  if (is_mixed(ctype)) {
     e = cudaMemcpy(p->tab_dev, mix.data(), p->tab_bytes, cudaMemcpyHostToDevice);
   } else if (ctype == kCF64) {
     e = cudaMemcpy(p->tab_dev, ht.tab.data(), p->tab_bytes, cudaMemcpyHostToDevice);

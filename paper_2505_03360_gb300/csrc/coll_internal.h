@@ -40,7 +40,9 @@ struct LayoutInfo {
 };
 
 // compute types of the collision kernel
-enum CType : int { kCF64 = 0, kCF32 = 1, kCDF = 2, kCMixF16 = 3 };
+enum CType : int { kCF64 = 0, kCF32 = 1, kCDF = 2, kCMixF16 = 3, kCMixBF16 = 4 };
+inline bool is_mixed(int ctype) { return ctype == kCMixF16 || ctype == kCMixBF16; }
+inline int mixed_parts(int ctype) { return ctype == kCMixBF16 ? 3 : 2; }
 
 #ifdef __CUDACC__
 #define COLL_HD __host__ __device__
@@ -101,9 +103,9 @@ int ragged_layout(int ctype, size_t* smem_bytes, size_t* ws_per_cta);
 int ragged_max_ctas_per_sm(int ctype, int* ctas);
 
 // Mixed-precision (tensor-core DFT-GEMM) collision kernel (mixed.cu)
-bool mixed_layout(int N, LayoutInfo* out);
-int launch_mixed(int N, bool io_f64, const CollArgs& a, int grid, void* stream);
-int mixed_max_ctas_per_sm(int N, bool io_f64, int* ctas);
+bool mixed_layout(int N, int parts, LayoutInfo* out);
+int launch_mixed(int N, bool io_f64, int parts, const CollArgs& a, int grid, void* stream);
+int mixed_max_ctas_per_sm(int N, bool io_f64, int parts, int* ctas);
 int mixed_set_drop_commit(int on);      // failure injection (coll_debug.h)
 
 // Moments kernel (moments.cu)
@@ -116,7 +118,7 @@ struct HostTables {
   std::vector<double> tab;    // [n_terms][N][N][N/2][2]
 };
 coll_status build_tables(const coll_plan_desc& d, HostTables* out);
-coll_status build_mixed_image(const HostTables& ht, int N, std::vector<unsigned char>* out);
+coll_status build_mixed_image(const HostTables& ht, int N, int parts, std::vector<unsigned char>* out);
 
 void count_launches(long long n);
 

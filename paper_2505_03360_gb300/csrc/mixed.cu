@@ -11,22 +11,26 @@
 // with D the real 2x2-block form of the N-point DFT matrix e^{+2 pi i k v / N}
 // (forward transforms by conjugating input and output).
 //
-// Precision (COLL_MIXED_F16X2): every operand is split into f16 parts,
-// x = x_h + x_l with x_h = f16(x), x_l = f16(x - x_h), and
-//   X D ~ (X_h + X_l) D_h + X_h D_l       (three products, FP32 accumulate)
-// which keeps about 22 significant bits per operand.  f16 has 5 exponent
-// bits, so each cell's data are scaled by powers of two: the input of a
-// three-pass transform is scaled to modulus <= 2^14 / N^3, which bounds every
-// intermediate (each pass grows the modulus by at most N) below 2^14.  The
-// bound of z_t's input uses max|F| (computed per cell) times max|A_t + iB_t|
-// (per term, from the plan).  Scales are undone exactly in FP32.
+// Precision.  Every operand is split into P parts of a 16-bit format:
+//   COLL_MIXED_F16X2  (P = 2, f16):  x = x_h + x_l,
+//                     X D ~ (X_h + X_l) D_h + X_h D_l                 (3 products)
+//   COLL_MIXED_BF16X3 (P = 3, bf16): x = x_h + x_m + x_l,
+//                     X D ~ (X_h + X_m + X_l) D_h + (X_h + X_m) D_m + X_h D_l  (6 products)
+// with FP32 accumulation; about 22 (f16) or 24 (bf16) significant bits per
+// operand.  f16 has 5 exponent bits, so each cell's data are scaled by powers
+// of two: the input of a three-pass transform is scaled to modulus
+// <= 2^14 / N^3, which bounds every intermediate (each pass grows the modulus
+// by at most N) below 2^14.  The bound of z_t's input uses max|F| (computed
+// per cell) times max|A_t + iB_t| (per term, from the plan).  Scales are powers
+// of two, undone exactly in FP32 (bf16 has FP32's exponent range and takes the
+// same scales).
 //
-// Layouts.  One pencil per row; a row holds the pencil's N complex inputs as
-// all hi parts, then all lo parts: K index 2N part + 2k + ri (f16 pairs
-// (re, im) per element and part).  The matrices, in the tensor core's K-major
-// 128-byte-swizzled shared-memory layout:
-//   B1[(v, ro)][(part, k, ri)] = D_h(ro, ri)(v, k)    over all 4N K  -> (X_h + X_l) D_h
-//   B2[(v, ro)][(k, ri)]       = D_l(ro, ri)(v, k)    over the first 2N K (the hi parts) -> X_h D_l
+// Layouts.  One pencil per row; a row holds the pencil's N complex inputs
+// part by part: K index 2N part + 2k + ri (16-bit pairs (re, im) per element
+// and part), padded to a multiple of 64.  Matrix s (s = 0 .. P-1) holds part s
+// of D in the tensor core's K-major 128-byte-swizzled shared-memory layout and
+// is applied to the first P - s parts of the operand:
+//   B_s[(v, ro)][(part, k, ri)] = D_s(ro, ri)(v, k),   part < P - s.
 // Passes per cell (row orders chosen so that, within a warp, the next pass's
 // K index varies fastest, which makes every epilogue store coalesced; F1 and
 // Y write back into the rows they read, so one pass buffer serves a cell):
@@ -51,6 +55,7 @@
 // memory (N^3 / 128 columns).  Every mbarrier wait is bounded; on expiry the
 // kernel records kStatusTimeout, stops issuing work, waits (bounded) for its
 // MMAs in flight, frees its tensor memory and returns.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -64,30 +69,62 @@ namespace coll {
 
 namespace {
 
-constexpr int kMixWG = 4;
-constexpr int kMixThreads = 128 * kMixWG;
+constexpr int kMixMaxWG = 4;
 
-template <int N> struct MixCfg {
+// Split of an FP32 complex value into P 16-bit parts per component, packed as
+// (re, im) pairs: w[p] = part p of (re, im).  Each residual is exact in FP32.
+template <int P> struct Split;
+template <> struct Split<2> {                 // f16 hi + lo
+  static constexpr uint32_t kFmt = 0;         // kind::f16 operand format: f16
+  static __device__ __forceinline__ void split(float re, float im, uint32_t (&w)[2]) {
+    const __half2 h = __floats2half2_rn(re, im);
+    const float2 hb = __half22float2(h);
+    const __half2 l = __floats2half2_rn(__fsub_rn(re, hb.x), __fsub_rn(im, hb.y));
+    w[0] = *reinterpret_cast<const uint32_t*>(&h);
+    w[1] = *reinterpret_cast<const uint32_t*>(&l);
+  }
+};
+template <> struct Split<3> {                 // bf16 hi + mid + lo
+  static constexpr uint32_t kFmt = 1;         // kind::f16 operand format: bf16
+  static __device__ __forceinline__ void split(float re, float im, uint32_t (&w)[3]) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+    const float2 hb = __bfloat1622float2(h);
+    const float r1 = __fsub_rn(re, hb.x), i1 = __fsub_rn(im, hb.y);
+    const __nv_bfloat162 m = __floats2bfloat162_rn(r1, i1);
+    const float2 mb = __bfloat1622float2(m);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(__fsub_rn(r1, mb.x), __fsub_rn(i1, mb.y));
+    w[0] = *reinterpret_cast<const uint32_t*>(&h);
+    w[1] = *reinterpret_cast<const uint32_t*>(&m);
+    w[2] = *reinterpret_cast<const uint32_t*>(&l);
+  }
+};
+
+template <int N, int P> struct MixCfg {
   static constexpr int H = N / 2;
-  static constexpr int KROW = 4 * N;                    // f16 per row
+  static constexpr int WG = P == 2 ? 4 : 3;             // warpgroups per CTA (shared memory bound)
+  static constexpr int THREADS = 128 * WG;
+  static constexpr int KP = 2 * N;                      // 16-bit values per part per row
+  static constexpr int KROW = (P * KP + 63) / 64 * 64;  // values per row, padded
   static constexpr int KB = KROW / 64;                  // 128-byte K blocks per row
   static constexpr int NOUT = 2 * N;                    // matrix rows (v, re/im)
   static constexpr int ROWS = N * N;                    // pencils of a full pass
-  static constexpr int RB = 8 * N;                      // bytes per row
+  static constexpr int RB = 2 * KROW;                   // bytes per row
+  static constexpr int PART_B = 2 * KP;                 // bytes per part in a row
   static constexpr int A_TILE = KB * 128 * 128;         // bytes of a 128-row A tile
-  static constexpr int KB2 = (2 * N + 63) / 64;         // K blocks of B2 (hi parts only)
-  static constexpr int B1_SET = KB * NOUT * 128;        // bytes of B1
-  static constexpr int B2_SET = KB2 * NOUT * 128;       // bytes of B2
-  static constexpr int B_SETS = B1_SET + B2_SET;
+  static constexpr int kb_of(int s) { return ((P - s) * KP + 63) / 64; }   // K blocks of matrix s
+  static constexpr int set_bytes(int s) { return kb_of(s) * NOUT * 128; }
+  static constexpr int set_off(int s) { return s == 0 ? 0 : set_off(s - 1) + set_bytes(s - 1); }
+  static constexpr int B_SETS = set_off(P);
   static constexpr int GCOLS = N * N * N / 128;         // tensor-memory columns of G
-  static constexpr int TCOLS_USED = kMixWG * NOUT + GCOLS;
+  static constexpr int TCOLS_USED = WG * NOUT + GCOLS;
   static constexpr int TCOLS = TCOLS_USED <= 32 ? 32 : TCOLS_USED <= 64 ? 64 : TCOLS_USED <= 128 ? 128
                              : TCOLS_USED <= 256 ? 256 : 512;
-  static constexpr int SMEM_USED = B_SETS + kMixWG * A_TILE + 1024;
+  static constexpr int SMEM_USED = B_SETS + WG * A_TILE + 1024;
   // enough shared memory that no more CTAs share an SM than its 512 tensor-memory columns hold
   static constexpr int SMEM_MIN = 233472 / (512 / TCOLS) - 4096;
   static constexpr int SMEM = SMEM_USED > SMEM_MIN ? SMEM_USED : SMEM_MIN;
   static_assert(N % 16 == 0 && ROWS % 128 == 0 && (H * N) % 128 == 0, "tile shape");
+  static_assert(WG <= kMixMaxWG, "warpgroups");
   static_assert(TCOLS_USED <= 512, "tensor memory");
   static_assert(B_SETS % 1024 == 0, "A tiles 1024-byte aligned");
   static_assert(SMEM <= 232448, "shared memory");
@@ -104,9 +141,10 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor, kind::f16: f16 A and B (K-major), FP32 accumulator
-__device__ __forceinline__ uint32_t idesc_f16(int m, int n) {
-  return (1u << 4) | (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(m >> 4) << 24);
+// instruction descriptor, kind::f16: A and B of format fmt (0 f16, 1 bf16), K-major, FP32 accumulator
+__device__ __forceinline__ uint32_t idesc_f16(int m, int n, uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
+         (static_cast<uint32_t>(m >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
@@ -186,18 +224,6 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// (re, im) -> (hi pair, lo pair) as two packed f16x2 words: hi = f16(x),
-// lo = f16(x - hi) (x - hi exact in FP32)
-__device__ __forceinline__ uint2 split2(float re, float im) {
-  const __half2 h = __floats2half2_rn(re, im);
-  const float2 hb = __half22float2(h);
-  const __half2 l = __floats2half2_rn(__fsub_rn(re, hb.x), __fsub_rn(im, hb.y));
-  uint2 r;
-  r.x = *reinterpret_cast<const uint32_t*>(&h);
-  r.y = *reinterpret_cast<const uint32_t*>(&l);
-  return r;
-}
-
 // shared-memory offset of byte b of tile row `row` (128-byte swizzle, 16 KB per K block)
 __device__ __forceinline__ uint32_t a_off(int row, int b) {
   return static_cast<uint32_t>((b >> 7) * 16384 + row * 128 + ((((b >> 4) & 7) ^ (row & 7)) << 4) + (b & 15));
@@ -222,7 +248,7 @@ enum MixPass : int { kMF2 = 0, kMF1, kMF0, kMX, kMY, kMZ };
 __device__ int g_mix_drop_commit = 0;
 
 struct MixShared {
-  uint64_t bar[kMixWG];
+  uint64_t bar[kMixMaxWG];
   uint32_t tbase;
   int abort;
   int drop_commit;
@@ -231,10 +257,12 @@ struct MixShared {
   float Fmax;
 };
 
-template <int N, typename Tio>
+template <int N, typename Tio, int P>
 struct MixCell {
-  using C = MixCfg<N>;
+  using C = MixCfg<N, P>;
+  using S = Split<P>;
   static constexpr int H = C::H;
+  static constexpr int kWG = C::WG;
 
   // cp.async of 128 rows (tile ti of the pass buffer) into the swizzled A tile
   static __device__ __forceinline__ void load_tile(const unsigned char* buf, int ti, int lt, uint32_t abase) {
@@ -259,22 +287,20 @@ struct MixCell {
     constexpr int rows = (pass == kMF1 || pass == kMF0) ? H * N : N * N;
     constexpr int nout = pass == kMF2 ? N : C::NOUT;
     const int q = lt >> 5;
-    for (int ti = wg; ti < rows / 128; ti += kMixWG) {
+    for (int ti = wg; ti < rows / 128; ti += kWG) {
       const int r = ti * 128 + lt;
       // ---- A tile
       if constexpr (pass == kMF2) {
         const Tio* fr = f + size_t(r) * N;
 #pragma unroll 1
         for (int k0 = 0; k0 < N; k0 += 4) {
-          uint32_t h[4], l[4];
+          uint32_t w[4][P];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const uint2 v = split2(float(double(fr[k0 + e]) * double(in_scale)), 0.0f);
-            h[e] = v.x;
-            l[e] = v.y;
-          }
-          *reinterpret_cast<uint4*>(atile + a_off(lt, 4 * k0)) = make_uint4(h[0], h[1], h[2], h[3]);
-          *reinterpret_cast<uint4*>(atile + a_off(lt, 4 * N + 4 * k0)) = make_uint4(l[0], l[1], l[2], l[3]);
+          for (int e = 0; e < 4; ++e) S::split(float(double(fr[k0 + e]) * double(in_scale)), 0.0f, w[e]);
+#pragma unroll
+          for (int p = 0; p < P; ++p)
+            *reinterpret_cast<uint4*>(atile + a_off(lt, p * C::PART_B + 4 * k0)) =
+                make_uint4(w[0][p], w[1][p], w[2][p], w[3][p]);
         }
       } else if constexpr (pass == kMX) {
         // Row (k0, k1): z[k2] = (A + iB) F for k2 < N/2 from row (k0, k1) of F
@@ -295,25 +321,30 @@ struct MixCell {
           const int rp = ((N - k0) % N) * N + (N - k1) % N;
           const float4 F = __ldcg(F4 + size_t(rr) * JN + j), T = __ldg(T4 + size_t(rr) * JN + j);
           const float4 G = __ldcg(F4 + size_t(rp) * JN + j), U = __ldg(T4 + size_t(rp) * JN + j);
-          const uint2 a0 = split2(__fmul_rn(__fsub_rn(__fmul_rn(T.x, F.x), __fmul_rn(T.y, F.y)), in_scale),
-                                  __fmul_rn(__fadd_rn(__fmul_rn(T.x, F.y), __fmul_rn(T.y, F.x)), in_scale));
-          const uint2 a1 = split2(__fmul_rn(__fsub_rn(__fmul_rn(T.z, F.z), __fmul_rn(T.w, F.w)), in_scale),
-                                  __fmul_rn(__fadd_rn(__fmul_rn(T.z, F.w), __fmul_rn(T.w, F.z)), in_scale));
-          *reinterpret_cast<uint2*>(atile + a_off(row, 8 * j)) = make_uint2(a0.x, a1.x);
-          *reinterpret_cast<uint2*>(atile + a_off(row, 4 * N + 8 * j)) = make_uint2(a0.y, a1.y);
+          uint32_t a0[P], a1[P], b0[P], b1[P];
+          S::split(__fmul_rn(__fsub_rn(__fmul_rn(T.x, F.x), __fmul_rn(T.y, F.y)), in_scale),
+                   __fmul_rn(__fadd_rn(__fmul_rn(T.x, F.y), __fmul_rn(T.y, F.x)), in_scale), a0);
+          S::split(__fmul_rn(__fsub_rn(__fmul_rn(T.z, F.z), __fmul_rn(T.w, F.w)), in_scale),
+                   __fmul_rn(__fadd_rn(__fmul_rn(T.z, F.w), __fmul_rn(T.w, F.z)), in_scale), a1);
           // partner: k2 = N - 2j - 1 and (j > 0) N - 2j, with conj(F)
-          const uint2 b1 = split2(__fmul_rn(__fadd_rn(__fmul_rn(U.z, G.z), __fmul_rn(U.w, G.w)), in_scale),
-                                  __fmul_rn(__fsub_rn(__fmul_rn(U.w, G.z), __fmul_rn(U.z, G.w)), in_scale));
+          S::split(__fmul_rn(__fadd_rn(__fmul_rn(U.z, G.z), __fmul_rn(U.w, G.w)), in_scale),
+                   __fmul_rn(__fsub_rn(__fmul_rn(U.w, G.z), __fmul_rn(U.z, G.w)), in_scale), b1);
+          if (j > 0) {
+            S::split(__fmul_rn(__fadd_rn(__fmul_rn(U.x, G.x), __fmul_rn(U.y, G.y)), in_scale),
+                     __fmul_rn(__fsub_rn(__fmul_rn(U.y, G.x), __fmul_rn(U.x, G.y)), in_scale), b0);
+          } else {
+#pragma unroll
+            for (int p = 0; p < P; ++p) b0[p] = 0u;
+          }
           const int k2b = N - 2 * j - 1;
-          *reinterpret_cast<uint32_t*>(atile + a_off(row, 4 * k2b)) = b1.x;
-          *reinterpret_cast<uint32_t*>(atile + a_off(row, 4 * N + 4 * k2b)) = b1.y;
-          const uint2 b0 = j > 0 ? split2(__fmul_rn(__fadd_rn(__fmul_rn(U.x, G.x), __fmul_rn(U.y, G.y)), in_scale),
-                                          __fmul_rn(__fsub_rn(__fmul_rn(U.y, G.x), __fmul_rn(U.x, G.y)), in_scale))
-                                 : make_uint2(0u, 0u);
           // slot N - 2j for j > 0; for j == 0 the same store zeroes the Nyquist slot N/2
           const int k2a = j > 0 ? N - 2 * j : H;
-          *reinterpret_cast<uint32_t*>(atile + a_off(row, 4 * k2a)) = b0.x;
-          *reinterpret_cast<uint32_t*>(atile + a_off(row, 4 * N + 4 * k2a)) = b0.y;
+#pragma unroll
+          for (int p = 0; p < P; ++p) {
+            *reinterpret_cast<uint2*>(atile + a_off(row, p * C::PART_B + 8 * j)) = make_uint2(a0[p], a1[p]);
+            *reinterpret_cast<uint32_t*>(atile + a_off(row, p * C::PART_B + 4 * k2b)) = b1[p];
+            *reinterpret_cast<uint32_t*>(atile + a_off(row, p * C::PART_B + 4 * k2a)) = b0[p];
+          }
         }
       } else {
         if (ti == wg) load_tile(buf, ti, lt, abase);     // first tile; later ones were prefetched
@@ -321,21 +352,20 @@ struct MixCell {
       }
       fence_async_smem();
       wg_sync(wg);
-      // ---- MMAs: (X_h + X_l) D_h + X_h D_l
+      // ---- MMAs: matrix s (part s of D) against the first P - s parts of the operand
       if (lt == 0) {
         fence_after();
-        const uint32_t id = idesc_f16(128, nout);
+        const uint32_t id = idesc_f16(128, nout, S::kFmt);
         uint32_t acc = 0;
 #pragma unroll
-        for (int kk = 0; kk < C::KB * 4; ++kk) {          // B1 over all 4N K: (X_h + X_l) D_h
-          mma_f16(tacc, sw128_desc(abase + (kk >> 2) * 16384 + (kk & 3) * 32),
-                  sw128_desc(bbase + (kk >> 2) * (C::NOUT * 128) + (kk & 3) * 32), id, acc);
-          acc = 1;
-        }
+        for (int sp = 0; sp < P; ++sp) {
 #pragma unroll
-        for (int kk = 0; kk < 2 * N / 16; ++kk)           // B2 over the hi parts: X_h D_l
-          mma_f16(tacc, sw128_desc(abase + (kk >> 2) * 16384 + (kk & 3) * 32),
-                  sw128_desc(bbase + C::B1_SET + (kk >> 2) * (C::NOUT * 128) + (kk & 3) * 32), id, 1u);
+          for (int kk = 0; kk < (P - sp) * C::KP / 16; ++kk) {
+            mma_f16(tacc, sw128_desc(abase + (kk >> 2) * 16384 + (kk & 3) * 32),
+                    sw128_desc(bbase + C::set_off(sp) + (kk >> 2) * (C::NOUT * 128) + (kk & 3) * 32), id, acc);
+            acc = 1;
+          }
+        }
         if (wg == 0 && sh.drop_commit) sh.drop_commit = 0;   // injected failure: no completion signal
         else mma_commit(&sh.bar[wg]);
       }
@@ -348,7 +378,7 @@ struct MixCell {
       fence_after();
       // the MMAs have read the A tile: start copying this warpgroup's next tile
       // of the pass so that the copy overlaps the epilogue
-      if (pass != kMF2 && pass != kMX && ti + kMixWG < rows / 128) load_tile(buf, ti + kMixWG, lt, abase);
+      if (pass != kMF2 && pass != kMX && ti + kWG < rows / 128) load_tile(buf, ti + kWG, lt, abase);
       // ---- epilogue: thread = TMEM lane = pencil row r
       const uint32_t lane_base = static_cast<uint32_t>(32 * q) << 16;
       for (int c0 = 0; c0 < nout; c0 += 32) {
@@ -403,10 +433,11 @@ struct MixCell {
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             if (e >= ne) break;
-            const uint2 s = split2(__uint_as_float(a[2 * e]), __uint_as_float(a[2 * e + 1]));
+            uint32_t w[P];
+            S::split(__uint_as_float(a[2 * e]), __uint_as_float(a[2 * e + 1]), w);
             unsigned char* rowp = base0 + size_t(e) * dstride * C::RB;
-            *reinterpret_cast<uint32_t*>(rowp) = s.x;
-            *reinterpret_cast<uint32_t*>(rowp + 4 * N) = s.y;
+#pragma unroll
+            for (int p = 0; p < P; ++p) *reinterpret_cast<uint32_t*>(rowp + p * C::PART_B) = w[p];
           }
         }
       }
@@ -435,7 +466,7 @@ struct MixCell {
 
     // max |f| for the forward scale
     float m = 0.0f;
-    for (int i = tid; i < N * N * N; i += kMixThreads) m = fmaxf(m, float(fabs(double(f[i]))));
+    for (int i = tid; i < N * N * N; i += C::THREADS) m = fmaxf(m, float(fabs(double(f[i]))));
     if (tid == 0) { sh.fmax = 0.0f; sh.Fmax = 0.0f; }
     __syncthreads();
     atomic_max_nonneg(&sh.fmax, m);
@@ -471,9 +502,9 @@ struct MixCell {
   }
 };
 
-template <int N, typename Tio>
-__global__ void __launch_bounds__(kMixThreads, 1) mixed_kernel(CollArgs a) {
-  using C = MixCfg<N>;
+template <int N, typename Tio, int P>
+__global__ void __launch_bounds__(MixCfg<N, P>::THREADS, 1) mixed_kernel(CollArgs a) {
+  using C = MixCfg<N, P>;
   extern __shared__ __align__(1024) unsigned char smraw[];
   __shared__ MixShared sh;
   const int tid = threadIdx.x, warp = tid >> 5, wg = tid >> 7;
@@ -485,7 +516,8 @@ __global__ void __launch_bounds__(kMixThreads, 1) mixed_kernel(CollArgs a) {
 
   // matrices: copy the pre-swizzled image
   const unsigned char* img = static_cast<const unsigned char*>(a.tab) + mixed_img_offset(N, a.n_terms);
-  for (int i = tid; i < C::B_SETS / 16; i += kMixThreads)
+  static_assert(C::B_SETS % 16 == 0, "matrix image copied in 16-byte pieces");
+  for (int i = tid; i < C::B_SETS / 16; i += C::THREADS)
     reinterpret_cast<uint4*>(sm)[i] = __ldg(reinterpret_cast<const uint4*>(img) + i);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&sh.tbase)),
@@ -493,7 +525,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) mixed_kernel(CollArgs a) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int w = 0; w < kMixWG; ++w)
+    for (int w = 0; w < C::WG; ++w)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&sh.bar[w])), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     sh.abort = 0;
@@ -505,7 +537,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) mixed_kernel(CollArgs a) {
   fence_after();
   const uint32_t tbase = sh.tbase;
   const uint32_t tacc = tbase + wg * C::NOUT;
-  const uint32_t tG = tbase + kMixWG * C::NOUT;
+  const uint32_t tG = tbase + C::WG * C::NOUT;
   uint32_t phase = 0;
   bool pending = false, bad = false;
   const auto* tab = static_cast<const float2*>(a.tab);
@@ -515,7 +547,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) mixed_kernel(CollArgs a) {
   for (long long c = blockIdx.x; c < a.n_cells; c += gridDim.x) {
     const Tio* f = static_cast<const Tio*>(a.f) + size_t(c) * N * N * N;
     Tio* Q = static_cast<Tio*>(a.Q) + size_t(c) * N * N * N;
-    if (MixCell<N, Tio>::cell(f, Q, tab, tmax, a.n_terms, ws, sm + C::B_SETS + wg * C::A_TILE, abase, bbase, tacc, tG, phase, pending, sh, bad))
+    if (MixCell<N, Tio, P>::cell(f, Q, tab, tmax, a.n_terms, ws, sm + C::B_SETS + wg * C::A_TILE, abase, bbase, tacc, tG, phase, pending, sh, bad))
       break;
   }
   // a wait that expired may leave this warpgroup's last MMA batch in flight
@@ -529,22 +561,24 @@ __global__ void __launch_bounds__(kMixThreads, 1) mixed_kernel(CollArgs a) {
   }
 }
 
-template <int N, typename Tio>
+template <int N, typename Tio, int P>
 int launch_mixed_t(const CollArgs& a, int grid, cudaStream_t st) {
-  auto k = mixed_kernel<N, Tio>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, MixCfg<N>::SMEM);
+  using C = MixCfg<N, P>;
+  auto k = mixed_kernel<N, Tio, P>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
   if (e != cudaSuccess) return int(e);
-  k<<<grid, kMixThreads, MixCfg<N>::SMEM, st>>>(a);
+  k<<<grid, C::THREADS, C::SMEM, st>>>(a);
   return int(cudaGetLastError());
 }
 
-template <int N, typename Tio>
+template <int N, typename Tio, int P>
 int occupancy_mixed_t(int* ctas) {
-  auto k = mixed_kernel<N, Tio>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, MixCfg<N>::SMEM);
+  using C = MixCfg<N, P>;
+  auto k = mixed_kernel<N, Tio, P>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
   if (e != cudaSuccess) return int(e);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k, kMixThreads, MixCfg<N>::SMEM);
-  const int by_tmem = 512 / MixCfg<N>::TCOLS;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k, C::THREADS, C::SMEM);
+  const int by_tmem = 512 / C::TCOLS;
   if (*ctas > by_tmem) *ctas = by_tmem;
   return int(e);
 }
@@ -561,6 +595,20 @@ double half_value(uint16_t b) {
   std::memcpy(&h, &b, 2);
   return double(__half2float(h));
 }
+// bfloat16: round the FP32 value to nearest even (host)
+uint16_t bf16_bits(double x) {
+  const float f = float(x);
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return uint16_t(u >> 16);
+}
+double bf16_value(uint16_t b) {
+  const uint32_t u = uint32_t(b) << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return double(f);
+}
 
 }  // namespace
 
@@ -569,45 +617,58 @@ int mixed_set_drop_commit(int on) {
   return int(cudaMemcpyToSymbol(g_mix_drop_commit, &v, sizeof(int)));
 }
 
-bool mixed_layout(int N, LayoutInfo* out) {
-  if (N != 16 && N != 32) return false;
+bool mixed_layout(int N, int parts, LayoutInfo* out) {
+  if ((N != 16 && N != 32) || (parts != 2 && parts != 3)) return false;
   LayoutInfo i;
   i.N = N;
   i.S0 = 1;
-  i.threads = kMixThreads;
+  i.threads = parts == 2 ? MixCfg<16, 2>::THREADS : MixCfg<16, 3>::THREADS;
   i.fh_smem = false;
   i.w_smem = false;
   i.g_smem = true;
+  const size_t rb = parts == 2 ? (N == 16 ? MixCfg<16, 2>::RB : MixCfg<32, 2>::RB)
+                               : (N == 16 ? MixCfg<16, 3>::RB : MixCfg<32, 3>::RB);
   i.fh_bytes = size_t(N) * (N / 2) * N * 8;        // forward half spectrum (FP32 complex)
-  i.w_bytes = size_t(N) * N * 8 * N;               // one pass buffer
+  i.w_bytes = size_t(N) * N * rb;                  // one pass buffer
   i.g_bytes = 0;                                   // the gain accumulator lives in tensor memory
   *out = i;
   return true;
 }
 
-int launch_mixed(int N, bool io_f64, const CollArgs& a, int grid, void* stream) {
+int launch_mixed(int N, bool io_f64, int parts, const CollArgs& a, int grid, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (N == 16) return io_f64 ? launch_mixed_t<16, double>(a, grid, st) : launch_mixed_t<16, float>(a, grid, st);
-  if (N == 32) return io_f64 ? launch_mixed_t<32, double>(a, grid, st) : launch_mixed_t<32, float>(a, grid, st);
+  if (parts == 2) {
+    if (N == 16) return io_f64 ? launch_mixed_t<16, double, 2>(a, grid, st) : launch_mixed_t<16, float, 2>(a, grid, st);
+    if (N == 32) return io_f64 ? launch_mixed_t<32, double, 2>(a, grid, st) : launch_mixed_t<32, float, 2>(a, grid, st);
+  } else if (parts == 3) {
+    if (N == 16) return io_f64 ? launch_mixed_t<16, double, 3>(a, grid, st) : launch_mixed_t<16, float, 3>(a, grid, st);
+    if (N == 32) return io_f64 ? launch_mixed_t<32, double, 3>(a, grid, st) : launch_mixed_t<32, float, 3>(a, grid, st);
+  }
   return int(cudaErrorInvalidValue);
 }
 
-int mixed_max_ctas_per_sm(int N, bool io_f64, int* ctas) {
-  if (N == 16) return io_f64 ? occupancy_mixed_t<16, double>(ctas) : occupancy_mixed_t<16, float>(ctas);
-  if (N == 32) return io_f64 ? occupancy_mixed_t<32, double>(ctas) : occupancy_mixed_t<32, float>(ctas);
+int mixed_max_ctas_per_sm(int N, bool io_f64, int parts, int* ctas) {
+  if (parts == 2) {
+    if (N == 16) return io_f64 ? occupancy_mixed_t<16, double, 2>(ctas) : occupancy_mixed_t<16, float, 2>(ctas);
+    if (N == 32) return io_f64 ? occupancy_mixed_t<32, double, 2>(ctas) : occupancy_mixed_t<32, float, 2>(ctas);
+  } else if (parts == 3) {
+    if (N == 16) return io_f64 ? occupancy_mixed_t<16, double, 3>(ctas) : occupancy_mixed_t<16, float, 3>(ctas);
+    if (N == 32) return io_f64 ? occupancy_mixed_t<32, double, 3>(ctas) : occupancy_mixed_t<32, float, 3>(ctas);
+  }
   return int(cudaErrorInvalidValue);
 }
 
 // Device image of a mixed plan: per-term tables [t][k0][k1][k2h] (A, B) as
-// float2, per-term max |A + iB| (rounded up), then the swizzled f16 matrices
-// B1 (hi, applied to both parts of the operand) and B2 (lo, applied to the hi
-// parts) of the inverse N-point DFT.
-coll_status build_mixed_image(const HostTables& ht, int N, std::vector<unsigned char>* out) {
+// float2, per-term max |A + iB| (rounded up), then the swizzled 16-bit
+// matrices B_s (part s of the inverse N-point DFT matrix, applied to the first
+// parts - s parts of the operand).
+coll_status build_mixed_image(const HostTables& ht, int N, int parts, std::vector<unsigned char>* out) {
   const int H = N / 2, nt = ht.n_terms;
   const size_t img_off = mixed_img_offset(N, nt);
-  const int KROW = 4 * N, KB = KROW / 64, KB2 = (2 * N + 63) / 64, NOUT = 2 * N;
-  const size_t b1 = size_t(KB) * NOUT * 128, b2 = size_t(KB2) * NOUT * 128;
-  out->assign(img_off + b1 + b2, 0);
+  const int KP = 2 * N, NOUT = 2 * N, P = parts;
+  size_t set_off[4] = {0, 0, 0, 0};
+  for (int sp = 0; sp < P; ++sp) set_off[sp + 1] = set_off[sp] + size_t(((P - sp) * KP + 63) / 64) * NOUT * 128;
+  out->assign(img_off + set_off[P], 0);
   float2* tab = reinterpret_cast<float2*>(out->data());
   float* tmax = reinterpret_cast<float*>(out->data() + mixed_tmax_offset(N, nt));
   for (int t = 0; t < nt; ++t) {
@@ -632,16 +693,24 @@ coll_status build_mixed_image(const HostTables& ht, int N, std::vector<unsigned 
   };
   for (int j = 0; j < NOUT; ++j) {
     const int v = j >> 1, ro = j & 1;
-    for (int kk = 0; kk < 2 * N; ++kk) {
+    for (int kk = 0; kk < KP; ++kk) {
       const int k = kk >> 1, ri = kk & 1;
       const double th = two_pi * double((size_t(k) * v) % N) / double(N);
       const double c = std::cos(th), sn = std::sin(th);
       // [[cos, -sin], [sin, cos]] for y = sum e^{+i th} x
       const double d = ro == 0 ? (ri == 0 ? c : -sn) : (ri == 0 ? sn : c);
-      const uint16_t hb = half_bits(d);
-      put(0, j, kk, hb);                 // B1, hi parts
-      put(0, j, 2 * N + kk, hb);         // B1, lo parts
-      put(b1, j, kk, half_bits(d - half_value(hb)));   // B2
+      uint16_t part[3];
+      if (P == 2) {
+        part[0] = half_bits(d);
+        part[1] = half_bits(d - half_value(part[0]));
+      } else {
+        part[0] = bf16_bits(d);
+        const double r1 = d - bf16_value(part[0]);
+        part[1] = bf16_bits(r1);
+        part[2] = bf16_bits(r1 - bf16_value(part[1]));
+      }
+      for (int sp = 0; sp < P; ++sp)
+        for (int q = 0; q < P - sp; ++q) put(set_off[sp], j, q * KP + kk, part[sp]);
     }
   }
   return COLL_OK;
