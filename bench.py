@@ -52,7 +52,8 @@ def fp64_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
 KERNEL_SOURCES = {
     "collision_f64_n32": ["collision_impl.cuh", "collision_layout.cuh", "fft.cuh", "twiddles.h", "coll_inst_d32.cu"],
     "moments_f64": ["moments.cu"],
-    "mixed_f16_n32": ["mixed.cu"],
+    "mixed_f16_n32": ["mixed.cu", "tcgen05.cuh"],
+    "mixed_sliced_n32": ["sliced.cu", "tcgen05.cuh", "dfloat.cuh"],
 }
 
 
@@ -62,6 +63,17 @@ def mixed_mma_flops_per_cell(N: int, n_terms: int) -> float:
     the lo matrix, each 2 * 128 * n_out * 16 flops (n_out = 2N, N for the real
     first forward pass)."""
     steps = 4 * N // 16 + 2 * N // 16
+    per = lambda nout: steps * 2.0 * 128 * nout * 16
+    tiles_f2 = N * N // 128
+    tiles_full = 2 * (N // 2) * N // 128 + 3 * n_terms * N * N // 128
+    return tiles_f2 * per(N) + tiles_full * per(2 * N)
+
+
+def sliced_mma_flops_per_cell(N: int, n_terms: int) -> float:
+    """Executed tensor-core flops of the fixed-point-slice path per cell: 128-row
+    tiles; per tile ten slice products of (2N/16) K steps, each 2 * 128 * n_out
+    * 16 flops (n_out = 2N, N for the real first forward pass)."""
+    steps = 10 * (2 * N // 16)
     per = lambda nout: steps * 2.0 * 128 * nout * 16
     tiles_f2 = N * N // 128
     tiles_full = 2 * (N // 2) * N // 128 + 3 * n_terms * N * N // 128
@@ -417,6 +429,25 @@ def run_ours(args, rank, world, local_rank):
     cell_errb = torch.linalg.vector_norm((Qm - Q).reshape(n, -1), dim=1) / torch.linalg.vector_norm(Q.reshape(n, -1), dim=1)
     errb = float(torch.linalg.vector_norm(Qm - Q) / torch.linalg.vector_norm(Q))
     planb.close()
+    # fixed-point-slice tensor-core variant (exact leading products, float-pair intermediates)
+    plans = coll.Plan(N, w["L"], lam=w["lam"], M=w["M"], Mtheta=w["Mtheta"], Mr=w["Mr"], prec="mixed_sliced",
+                      io_dtype=0, max_cells=n, device=dev)
+    wss = plans.reserve(n)
+    with torch.cuda.stream(stream):
+        coll.coll_eval_batch(plans.handle, f, Qm, n, wss, stream=stream)
+    torch.cuda.synchronize(dev)
+    as_, bs_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    as_.record(stream)
+    for _ in range(args.steps):
+        coll.coll_eval_batch(plans.handle, f, Qm, n, wss, stream=stream)
+    bs_.record(stream)
+    torch.cuda.synchronize(dev)
+    ts = as_.elapsed_time(bs_) / 1e3 / args.steps
+    assert plans.status() == coll.COLL_OK
+    cell_errs = torch.linalg.vector_norm((Qm - Q).reshape(n, -1), dim=1) / torch.linalg.vector_norm(Q.reshape(n, -1), dim=1)
+    errs = float(torch.linalg.vector_norm(Qm - Q) / torch.linalg.vector_norm(Q))
+    n_terms_s = plans.n_terms
+    plans.close()
     del Qm
 
     if rank != 0:
@@ -474,7 +505,22 @@ def run_ours(args, rank, world, local_rank):
                          "value": n / tb, "unit": "cell-evals/s", "rel_l2_vs_f64": errb,
                          "cell_rel_l2_median": float(cell_errb.median()), "cell_rel_l2_max": float(cell_errb.max()),
                          "ms_per_launch": 1e3 * tb, "speedup_vs_f64": coll_ms / (1e3 * tb),
-                         "arithmetic": "DFT-GEMMs on tcgen05 tensor cores, bf16 hi+mid+lo operands, FP32 accumulate"}},
+                         "arithmetic": "DFT-GEMMs on tcgen05 tensor cores, bf16 hi+mid+lo operands, FP32 accumulate"},
+                     "mixed_sliced": {
+                         "value": n / ts, "unit": "cell-evals/s", "rel_l2_vs_f64": errs,
+                         "cell_rel_l2_median": float(cell_errs.median()), "cell_rel_l2_max": float(cell_errs.max()),
+                         "ms_per_launch": 1e3 * ts, "speedup_vs_f64": coll_ms / (1e3 * ts),
+                         "arithmetic": "DFT-GEMMs on tcgen05 tensor cores, fixed-point f16 slices (three 9-bit "
+                                       "integer parts + f16 tail), two leading product levels summed exactly in "
+                                       "FP32 tensor memory, float-pair intermediates",
+                         "roofline": {"bound": "tensor", "achieved": sliced_mma_flops_per_cell(N, n_terms_s) * n / ts / 1e12,
+                                      "peak": tc_peak, "unit": "TFLOP/s",
+                                      "frac": (sliced_mma_flops_per_cell(N, n_terms_s) * n / ts / 1e12 / tc_peak)
+                                      if tc_peak else None,
+                                      "peak_basis": "measured dense bf16 burst (f16 runs at the same dense rate)",
+                                      "executed_mma_flops_per_launch": sliced_mma_flops_per_cell(N, n_terms_s) * n,
+                                      "traffic": load_traffic("mixed_sliced_n32"),
+                                      "algorithmic_tflops": flops / ts / 1e12}}},
         "moments": {"kernel": "moments sums + scalar finish (2 launches)", "ms_per_launch": mom_ms,
                     "achieved_gbs": mom_bytes / (mom_ms / 1e3) / 1e9, "peak_gbs": peaks.get("hbm_gbs"),
                     "frac": (mom_bytes / (mom_ms / 1e3) / 1e9 / peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None,
@@ -520,7 +566,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=100,
                     help="requests of the serving stream measured beside the main line (0: skip)")
     ap.add_argument("--serve-max-cells", type=int, default=64)
-    ap.add_argument("--prec", default="f64", choices=["f64", "f32x2", "f32", "mixed_f16x2"],
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32x2", "f32", "mixed_f16x2", "mixed_bf16x3",
+                                                      "mixed_sliced"],
                     help="compute precision of the main path in --profile-only runs")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

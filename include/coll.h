@@ -62,15 +62,24 @@ typedef enum {
                              N = 16, 32; not in ragged launches              */
   COLL_MIXED_BF16X3 = 3,  /* the same with bf16 hi+mid+lo operands (6
                              products); N = 16, 32; not in ragged launches   */
-  COLL_F32X2 = 4          /* transforms in float pairs (hi + lo, ~48 bits) on
+  COLL_F32X2 = 4,         /* transforms in float pairs (hi + lo, ~48 bits) on
                              the FP32 pipe; N = 16, 24, 32                    */
+  COLL_MIXED_SLICED = 5   /* every transform a DFT-GEMM on the tensor cores
+                             with fixed-point f16 operand slices (three 9-bit
+                             integer parts and an f16 tail per value); the two
+                             leading product levels are summed exactly by the
+                             FP32 accumulator, intermediates are float pairs:
+                             about 38 significant bits per transform (relative
+                             L2 error ~1e-8 against FP64); N = 16, 32; not in
+                             ragged launches                                   */
 } coll_precision;
 
 /*
  * Plan descriptor (sec. 4.4.1 "The 3d case", with the readings listed in the
  * design notes):
  *   N        points per velocity axis; 16, 24, 32, 48 or 64 (FP64 and
- *            COLL_F32X2: 16, 24, 32; tensor-core precisions: 16, 32)
+ *            COLL_F32X2: 16, 24, 32; tensor-core precisions COLL_MIXED_*:
+ *            16, 32)
  *   L        half-width of the periodic velocity box [-L, L)^3
  *   S        support radius; truncation R = 2S (sec. 4.4.1, Q^R);
  *            0 selects S = 2L / (3 + sqrt 2), the no-overlap bound

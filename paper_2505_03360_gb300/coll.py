@@ -19,9 +19,9 @@ HEADER = os.path.join(os.path.dirname(PKG), "include", "coll.h")
 HEADERS = [HEADER, os.path.join(os.path.dirname(PKG), "include", "coll_debug.h")]
 
 COLL_OK, COLL_EINVAL, COLL_EUNSUPPORTED, COLL_ENOMEM, COLL_ECUDA, COLL_ETIMEOUT, COLL_ENONFINITE = range(7)
-COLL_F64, COLL_F32, COLL_MIXED_F16X2, COLL_MIXED_BF16X3, COLL_F32X2 = range(5)
+COLL_F64, COLL_F32, COLL_MIXED_F16X2, COLL_MIXED_BF16X3, COLL_F32X2, COLL_MIXED_SLICED = range(6)
 PREC = {"f64": COLL_F64, "f32": COLL_F32, "mixed_f16x2": COLL_MIXED_F16X2,
-        "mixed_bf16x3": COLL_MIXED_BF16X3, "f32x2": COLL_F32X2}
+        "mixed_bf16x3": COLL_MIXED_BF16X3, "f32x2": COLL_F32X2, "mixed_sliced": COLL_MIXED_SLICED}
 
 
 class CollError(RuntimeError):

@@ -149,13 +149,14 @@ coll_status coll_plan_create(const coll_plan_desc* desc, coll_plan* out) {
       (d.sphere_rule != 0 && d.sphere_rule != 1) || (d.dealias != 0 && d.dealias != 1))
     return COLL_EINVAL;
   if (d.prec != COLL_F64 && d.prec != COLL_F32 && d.prec != COLL_MIXED_F16X2 && d.prec != COLL_MIXED_BF16X3 &&
-      d.prec != COLL_F32X2)
+      d.prec != COLL_F32X2 && d.prec != COLL_MIXED_SLICED)
     return COLL_EINVAL;
   if (d.dealias) return COLL_EUNSUPPORTED;
   const int ctype = d.prec == COLL_F64 ? kCF64
                   : d.prec == COLL_F32 ? kCF32
                   : d.prec == COLL_MIXED_F16X2 ? kCMixF16
-                  : d.prec == COLL_MIXED_BF16X3 ? kCMixBF16 : kCDF;
+                  : d.prec == COLL_MIXED_BF16X3 ? kCMixBF16
+                  : d.prec == COLL_MIXED_SLICED ? kCMixSliced : kCDF;
   if (!valid_N(d.N, ctype)) return COLL_EUNSUPPORTED;
 
   HostTables ht;
@@ -184,7 +185,8 @@ coll_status coll_plan_create(const coll_plan_desc* desc, coll_plan* out) {
   const size_t n = ht.tab.size();
   std::vector<unsigned char> mix;
   if (is_mixed(ctype)) {
-    st = build_mixed_image(ht, d.N, mixed_parts(ctype), &mix);
+    st = ctype == kCMixSliced ? build_sliced_image(ht, d.N, &mix)
+                              : build_mixed_image(ht, d.N, mixed_parts(ctype), &mix);
     if (st != COLL_OK) { delete p; return st; }
     p->tab_bytes = mix.size();
   } else {

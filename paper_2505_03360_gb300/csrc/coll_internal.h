@@ -40,8 +40,9 @@ struct LayoutInfo {
 };
 
 // compute types of the collision kernel
-enum CType : int { kCF64 = 0, kCF32 = 1, kCDF = 2, kCMixF16 = 3, kCMixBF16 = 4 };
-inline bool is_mixed(int ctype) { return ctype == kCMixF16 || ctype == kCMixBF16; }
+enum CType : int { kCF64 = 0, kCF32 = 1, kCDF = 2, kCMixF16 = 3, kCMixBF16 = 4, kCMixSliced = 5 };
+// tensor-core compute types (N = 16 and 32, no ragged launches)
+inline bool is_mixed(int ctype) { return ctype == kCMixF16 || ctype == kCMixBF16 || ctype == kCMixSliced; }
 inline int mixed_parts(int ctype) { return ctype == kCMixBF16 ? 3 : 2; }
 
 #ifdef __CUDACC__
@@ -55,6 +56,14 @@ COLL_HD inline size_t mixed_tab_bytes(int N, int n_terms) { return size_t(n_term
 COLL_HD inline size_t mixed_tmax_offset(int N, int n_terms) { return mixed_tab_bytes(N, n_terms); }
 COLL_HD inline size_t mixed_img_offset(int N, int n_terms) {
   return (mixed_tab_bytes(N, n_terms) + size_t(n_terms) * 4 + 1023) / 1024 * 1024;
+}
+
+// Device image of a sliced plan (sliced.cu): per-term tables as float pairs
+// (A_h, A_l, B_h, B_l), the per-term bound max|A + iB|, then the f16 matrices.
+COLL_HD inline size_t sliced_tab_bytes(int N, int n_terms) { return size_t(n_terms) * N * (N / 2) * N * 16; }
+COLL_HD inline size_t sliced_tmax_offset(int N, int n_terms) { return sliced_tab_bytes(N, n_terms); }
+COLL_HD inline size_t sliced_img_offset(int N, int n_terms) {
+  return (sliced_tab_bytes(N, n_terms) + size_t(n_terms) * 4 + 1023) / 1024 * 1024;
 }
 
 // Returns false if (N, ctype) has no kernel instantiation.
@@ -108,6 +117,11 @@ int launch_mixed(int N, bool io_f64, int parts, const CollArgs& a, int grid, voi
 int mixed_max_ctas_per_sm(int N, bool io_f64, int parts, int* ctas);
 int mixed_set_drop_commit(int on);      // failure injection (coll_debug.h)
 
+// Fixed-point-slice tensor-core collision kernel (sliced.cu)
+bool sliced_layout(int N, LayoutInfo* out);
+int launch_sliced(int N, bool io_f64, const CollArgs& a, int grid, void* stream);
+int sliced_max_ctas_per_sm(int N, bool io_f64, int* ctas);
+
 // Moments kernel (moments.cu)
 int launch_moments(const void* f, int io_f64, int N, double L, long long n_cells, double eta0,
                    double delta0, coll_moments* mom, uint8_t* mask, void* stream);
@@ -119,6 +133,7 @@ struct HostTables {
 };
 coll_status build_tables(const coll_plan_desc& d, HostTables* out);
 coll_status build_mixed_image(const HostTables& ht, int N, int parts, std::vector<unsigned char>* out);
+coll_status build_sliced_image(const HostTables& ht, int N, std::vector<unsigned char>* out);
 
 void count_launches(long long n);
 

@@ -32,7 +32,8 @@ template <int N, typename T> LayoutInfo make_info(int variant) {
 }
 
 bool layout_info(int N, int ctype, int variant, LayoutInfo* out) {
-  if (is_mixed(ctype)) return mixed_layout(N, mixed_parts(ctype), out);   // one shape for every variant
+  if (ctype == kCMixSliced) return sliced_layout(N, out);                    // one shape for every variant
+  if (is_mixed(ctype)) return mixed_layout(N, mixed_parts(ctype), out);
   if (ctype == kCDF) {
     switch (N) {
       case 16: *out = make_info<16, df>(variant); return true;
@@ -153,12 +154,14 @@ int ragged_max_ctas_per_sm(int ctype, int* ctas) {
 
 int launch_collision(int N, int ctype, bool io_f64, int variant, const CollArgs& a, int grid, void* stream) {
   count_launches(1);
+  if (ctype == kCMixSliced) return launch_sliced(N, io_f64, a, grid, stream);
   if (is_mixed(ctype)) return launch_mixed(N, io_f64, mixed_parts(ctype), a, grid, stream);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   COLL_DISPATCH(launch_one, a, grid, st)
 }
 
 int collision_max_ctas_per_sm(int N, int ctype, bool io_f64, int variant, int* ctas) {
+  if (ctype == kCMixSliced) return sliced_max_ctas_per_sm(N, io_f64, ctas);
   if (is_mixed(ctype)) return mixed_max_ctas_per_sm(N, io_f64, mixed_parts(ctype), ctas);
   COLL_DISPATCH(occupancy_one, ctas)
 }

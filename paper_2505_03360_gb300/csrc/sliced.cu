@@ -1,0 +1,563 @@
+// Fixed-point-slice tensor-core collision path (COLL_MIXED_SLICED).
+//
+// Same index-space algorithm and pass structure as mixed.cu (arxiv 2505.03360,
+// sec. 4.4.1: F = DFT3(f), z_t = IDFT3((A_t + i B_t) F), Q = sum_t Re z_t Im z_t,
+// the last term being the loss term), every 1D transform a DFT-GEMM on the
+// tcgen05 tensor cores, but with an operand encoding whose leading products
+// the tensor core's FP32 accumulator sums exactly, so that each transform
+// keeps about 38 significant bits instead of FP32's 24.
+//
+// Encoding.  Every real component x of a pass input is written, with
+// q = 2^(E-9) and 2^E above the maximum modulus of the pass input, as
+//     x = q (s0 + 2^-9 s1 + 2^-18 (s2 + sT)),
+// s0, s1, s2 integers (|s0| <= 512, |s1|, |s2| <= 256) and sT in [-1/2, 1/2]
+// rounded to f16; all four parts are f16 values (integers up to 2048 are exact
+// in f16).  The DFT matrix entries D (|D| <= 1) are split the same way with
+// q = 2^-9:  D = 2^-9 (d0 + 2^-9 d1 + 2^-18 (d2 + dT)).  Grouping the products
+// by level, x D / (q 2^-9) = L0 + 2^-9 L1 + 2^-18 L2 with
+//     L0 = s0 d0                                        (exact)
+//     L1 = s0 d1 + s1 d0                                (exact)
+//     L2 = s0 d2 + s1 d1 + s2 d0 + s0 dT + sT d0 + 2^-9 (s1 d2 + s2 d1)
+// f16 x f16 products are exact in FP32, and every partial sum of L0 and of L1
+// is an integer below 2^24 in modulus (|s0| sum_k |d0| <= 512 (512 N sqrt 2 + N)
+// and the like), so the FP32 accumulators of L0 and L1 are exact; only L2
+// rounds, at about 2^-42 of L0's scale.  The products left out are below 2^-45
+// of it.  Each level has its own tensor-memory accumulator; the epilogue
+// combines them into a float pair (hi + lo, about 48 bits).
+//
+// Intermediates: the forward spectrum F, the pass buffer and the gain
+// accumulator G are float pairs in the CTA's workspace (L2 resident), and the
+// term tables (A_t, B_t) are float pairs, so that nothing between the
+// transforms rounds to FP32.  The scale E of a pass is the maximum of its
+// input, taken by the previous pass's epilogue (the z_t input uses the bound
+// max|F| max|A_t + i B_t|, which both reach at k = 0).
+//
+// Layouts and row orders are those of mixed.cu.  A row of the A tile holds the
+// four parts one after another (K index 2N part + 2k + ri); the matrix image
+// holds d0, d1, d2, dT, 2^-9 d1, 2^-9 d2 one after another along K.  One CTA
+// per SM, persistent over cells; two warpgroups at N = 32 (shared memory:
+// 64 KB per A tile + 48 KB of matrices), four at N = 16; each warpgroup owns
+// three accumulators of 2N tensor-memory columns.  Every mbarrier wait is
+// bounded as in mixed.cu.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "coll_internal.h"
+#include "dfloat.cuh"
+#include "tcgen05.cuh"
+
+namespace coll {
+
+namespace {
+
+constexpr int kSlMaxWG = 4;
+constexpr int kSlParts = 4;      // s0, s1, s2, sT
+constexpr int kSlMats = 6;       // d0, d1, d2, dT, 2^-9 d1, 2^-9 d2
+constexpr int kSlPairs = 10;
+
+// A part and matrix of every product, in issue order: L0 = s0 d0; L1 = s0 d1 +
+// s1 d0; L2 = s0 d2 + s1 d1 + s2 d0 + s0 dT + sT d0 + s1 (2^-9 d2) + s2 (2^-9 d1)
+__host__ __device__ constexpr int sl_pair_a(int i) {
+  constexpr int v[kSlPairs] = {0, 0, 1, 0, 1, 2, 0, 3, 1, 2};
+  return v[i];
+}
+__host__ __device__ constexpr int sl_pair_b(int i) {
+  constexpr int v[kSlPairs] = {0, 1, 0, 2, 1, 0, 3, 0, 5, 4};
+  return v[i];
+}
+__host__ __device__ constexpr int sl_pair_acc(int i) { return i == 0 ? 0 : (i < 3 ? 1 : 2); }
+// the first product of each accumulator overwrites it
+__host__ __device__ constexpr bool sl_pair_first(int i) { return i == 0 || i == 1 || i == 3; }
+
+template <int N> struct SlCfg {
+  static constexpr int H = N / 2;
+  static constexpr int WG = N == 16 ? 4 : 2;               // warpgroups per CTA (shared memory bound)
+  static constexpr int THREADS = 128 * WG;
+  static constexpr int KP = 2 * N;                         // f16 values per part per row
+  static constexpr int KS = KP / 16;                       // 16-wide K steps per part
+  static constexpr int KROW = kSlParts * KP;               // values per A row
+  static constexpr int KB = KROW / 64;                     // 128-byte K blocks per A row
+  static constexpr int PART_B = 2 * KP;                    // bytes per part in an A row
+  static constexpr int NOUT = 2 * N;                       // matrix rows (v, re/im)
+  static constexpr int B_BYTES = (kSlMats * KP / 64) * NOUT * 128;
+  static constexpr int A_TILE = KB * 128 * 128;
+  static constexpr int TCOLS_USED = WG * 3 * NOUT;
+  static constexpr int TCOLS = 512;
+  static constexpr int SMEM = B_BYTES + WG * A_TILE + 1024;
+  static constexpr size_t F_BYTES = size_t(N) * N * H * 16;        // half spectrum, complex float pairs
+  static constexpr size_t BUF_BYTES = size_t(N) * N * N * 16;      // N^2 rows of N complex float pairs
+  static constexpr size_t G_BYTES = size_t(N) * N * N * 8;         // gain accumulator, float pairs
+  static_assert(KROW % 64 == 0 && (kSlMats * KP) % 64 == 0, "K blocks");
+  static_assert(TCOLS_USED <= TCOLS, "tensor memory");
+  static_assert(B_BYTES % 1024 == 0 && A_TILE % 1024 == 0, "1024-byte aligned tiles");
+  static_assert(SMEM <= 232448, "shared memory");
+  static_assert(WG <= kSlMaxWG, "warpgroups");
+};
+
+// Parts of t = th + tl (a float pair, |t| < 2^9): s0, s1, s2 integers and the
+// tail sT, with t = s0 + 2^-9 s1 + 2^-18 (s2 + sT).  Every step but the last
+// addition is exact.
+__device__ __forceinline__ void slice4(float th, float tl, float (&s)[4]) {
+  const float s0 = rintf(th);
+  const df r = two_sum(__fsub_rn(th, s0), tl);
+  const float a = __fmul_rn(r.h, 512.0f), al = __fmul_rn(r.l, 512.0f);
+  const float s1 = rintf(a);
+  const df u = two_sum(__fsub_rn(a, s1), al);
+  const float b = __fmul_rn(u.h, 512.0f), bl = __fmul_rn(u.l, 512.0f);
+  const float s2 = rintf(b);
+  s[0] = s0;
+  s[1] = s1;
+  s[2] = s2;
+  s[3] = __fadd_rn(__fsub_rn(b, s2), bl);
+}
+
+// value of one output component from the three level accumulators, times sc
+__device__ __forceinline__ df combine(uint32_t u0, uint32_t u1, uint32_t u2, float sc) {
+  const df s = two_sum(__uint_as_float(u0), __fmul_rn(__uint_as_float(u1), 0x1p-9f));
+  const float e = __fmaf_rn(__uint_as_float(u2), 0x1p-18f, s.l);
+  const df v = quick_two_sum(s.h, e);
+  return df{__fmul_rn(v.h, sc), __fmul_rn(v.l, sc)};
+}
+
+__device__ __forceinline__ df dmul(df a, float s) { return df{__fmul_rn(a.h, s), __fmul_rn(a.l, s)}; }
+
+// scale of a pass from the maximum modulus m of its input: in = 2^(9-E), out = 2^(E-18)
+__device__ __forceinline__ void pass_scales(float m, float* in, float* out) {
+  const int E = exp_of(__fmul_ru(m, 1.000001f));
+  *in = ldexpf(1.0f, 9 - E);
+  *out = ldexpf(1.0f, E - 18);
+}
+
+enum SlPass : int { kSF2 = 0, kSF1, kSF0, kSX, kSY, kSZ };
+
+struct SlShared {
+  uint64_t bar[kSlMaxWG];
+  uint32_t tbase;
+  int abort;
+  float pmax[2];        // maximum modulus of the current / next pass input
+  float Fmax;           // max (|Re F| + |Im F|)
+};
+
+template <int N, typename Tio>
+struct SlCell {
+  using C = SlCfg<N>;
+  static constexpr int H = C::H;
+  static constexpr int kWG = C::WG;
+
+  // parts of the complex value (re, im) (scaled float pairs) into slot k of A-tile row `row`
+  static __device__ __forceinline__ void put(unsigned char* atile, int row, int k, float rh, float rl, float ih,
+                                             float il) {
+    float a[4], b[4];
+    slice4(rh, rl, a);
+    slice4(ih, il, b);
+#pragma unroll
+    for (int p = 0; p < kSlParts; ++p) {
+      const __half2 h = __floats2half2_rn(a[p], b[p]);
+      *reinterpret_cast<uint32_t*>(atile + a_off(row, p * C::PART_B + 4 * k)) = *reinterpret_cast<const uint32_t*>(&h);
+    }
+  }
+
+  // first forward pass: rows (v0, v1) of f, real values at slots v2
+  static __device__ __forceinline__ void stage_f(const Tio* __restrict__ f, int ti, int lt, unsigned char* atile,
+                                                 float sc) {
+    constexpr int RPI = 128 / N;                 // rows per sweep of the warpgroup
+    const int k = lt % N;
+#pragma unroll 4
+    for (int it = 0; it < N; ++it) {
+      const int row = it * RPI + lt / N;
+      const Tio x = f[size_t(ti * 128 + row) * N + k];
+      df v;
+      if constexpr (sizeof(Tio) == 8) v = df_from_double(double(x));
+      else v = df{float(x), 0.0f};
+      put(atile, row, k, __fmul_rn(v.h, sc), __fmul_rn(v.l, sc), 0.0f, 0.0f);
+    }
+  }
+
+  // passes F1, F0, Y, Z: 128 rows of the pass buffer, one complex slot per lane
+  static __device__ __forceinline__ void stage_buf(const float4* buf, int ti, int lt, unsigned char* atile,
+                                                   float sc) {
+    constexpr int RPI = 128 / N;
+    const int k = lt % N;
+#pragma unroll 4
+    for (int it = 0; it < N; ++it) {
+      const int row = it * RPI + lt / N;
+      const float4 v = __ldcg(buf + size_t(ti * 128 + row) * N + k);
+      put(atile, row, k, __fmul_rn(v.x, sc), __fmul_rn(v.y, sc), __fmul_rn(v.z, sc), __fmul_rn(v.w, sc));
+    }
+  }
+
+  // pass X: row (k0, k1), slot k2: (A + iB) F for k2 < N/2 from row (k0, k1) of F
+  // and of the term table, for k2 > N/2 from the partner row (-k0, -k1) at
+  // N - k2 (conjugated F; the multipliers are even); slot N/2 is zero
+  static __device__ __forceinline__ void stage_x(const float4* Fs, const float4* __restrict__ tab_t, int ti,
+                                                 int lt, unsigned char* atile, float sc) {
+    constexpr int RPI = 128 / H;
+    const int k2 = lt % H;
+#pragma unroll 2
+    for (int it = 0; it < H; ++it) {
+      const int row = it * RPI + lt / H;
+      const int rr = ti * 128 + row;
+      const int k0 = rr / N, k1 = rr % N;
+      const int rp = ((N - k0) % N) * N + (N - k1) % N;
+      const float4 F = __ldcg(Fs + size_t(rr) * H + k2), T = __ldg(tab_t + size_t(rr) * H + k2);
+      const float4 G = __ldcg(Fs + size_t(rp) * H + k2), U = __ldg(tab_t + size_t(rp) * H + k2);
+      {
+        const df A{T.x, T.y}, B{T.z, T.w}, Fr{F.x, F.y}, Fi{F.z, F.w};
+        const df zr = dmul(A * Fr - B * Fi, sc), zi = dmul(A * Fi + B * Fr, sc);
+        put(atile, row, k2, zr.h, zr.l, zi.h, zi.l);
+      }
+      if (k2 > 0) {
+        const df A{U.x, U.y}, B{U.z, U.w}, Gr{G.x, G.y}, Gi{G.z, G.w};
+        const df zr = dmul(A * Gr + B * Gi, sc), zi = dmul(B * Gr - A * Gi, sc);
+        put(atile, row, N - k2, zr.h, zr.l, zi.h, zi.l);
+      } else {
+#pragma unroll
+        for (int p = 0; p < kSlParts; ++p)
+          *reinterpret_cast<uint32_t*>(atile + a_off(row, p * C::PART_B + 4 * H)) = 0u;
+      }
+    }
+  }
+
+  // One pass over this warpgroup's tiles.  Returns false (uniformly over the
+  // warpgroup) if an MMA wait expired; the expired phase stays pending.
+  template <int pass>
+  static __device__ __forceinline__ bool run(int wg, int lt, unsigned char* atile, uint32_t abase, uint32_t bbase,
+                                             uint32_t tacc, uint32_t& phase, bool& pending, SlShared& sh,
+                                             const Tio* __restrict__ f, Tio* __restrict__ Q, float4* Fs,
+                                             float4* buf, float2* G, const float4* __restrict__ tab_t, float sc_in,
+                                             float sc_out, float* next_max, bool first_term, bool last_term,
+                                             bool& bad) {
+    constexpr int rows = (pass == kSF1 || pass == kSF0) ? H * N : N * N;
+    constexpr int nout = pass == kSF2 ? N : C::NOUT;
+    const int q = lt >> 5;
+    float lmax = 0.0f;
+    for (int ti = wg; ti < rows / 128; ti += kWG) {
+      const int r = ti * 128 + lt;
+      // ---- A tile
+      if constexpr (pass == kSF2) stage_f(f, ti, lt, atile, sc_in);
+      else if constexpr (pass == kSX) stage_x(Fs, tab_t, ti, lt, atile, sc_in);
+      else stage_buf(buf, ti, lt, atile, sc_in);
+      fence_async_smem();
+      wg_sync(wg);
+      // ---- MMAs: ten products into three accumulators
+      if (lt == 0) {
+        fence_after();
+        const uint32_t id = idesc_f16(128, nout, 0);
+#pragma unroll
+        for (int pi = 0; pi < kSlPairs; ++pi) {
+          const int pa = sl_pair_a(pi), pb = sl_pair_b(pi), pc = sl_pair_acc(pi);
+          const bool first = sl_pair_first(pi);
+#pragma unroll
+          for (int j = 0; j < C::KS; ++j) {
+            const int ka = pa * C::KS + j, kb = pb * C::KS + j;
+            mma_f16(tacc + pc * C::NOUT, sw128_desc(abase + (ka >> 2) * 16384 + (ka & 3) * 32),
+                    sw128_desc(bbase + (kb >> 2) * (C::NOUT * 128) + (kb & 3) * 32), id,
+                    (first && j == 0) ? 0u : 1u);
+          }
+        }
+        mma_commit(&sh.bar[wg]);
+      }
+      if (!wg_all(wg, wait_parity(&sh.bar[wg], phase))) {
+        if (lt == 0) atomicExch(&sh.abort, 1);
+        pending = true;
+        return false;
+      }
+      phase ^= 1u;
+      fence_after();
+      // ---- epilogue: thread = TMEM lane = pencil row r
+      const uint32_t lane_base = static_cast<uint32_t>(32 * q) << 16;
+      for (int c0 = 0; c0 < nout; c0 += 16) {
+        uint32_t u0[16], u1[16], u2[16];
+        tld16_nw(tacc + lane_base + c0, u0);
+        tld16_nw(tacc + C::NOUT + lane_base + c0, u1);
+        tld16_nw(tacc + 2 * C::NOUT + lane_base + c0, u2);
+        tld_wait(u0);
+        tld_tie(u1);
+        tld_tie(u2);
+        const int v0c = c0 >> 1;                         // first complex output of this chunk
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const df re = combine(u0[2 * e], u1[2 * e], u2[2 * e], sc_out);
+          const df im = combine(u0[2 * e + 1], u1[2 * e + 1], u2[2 * e + 1], sc_out);
+          const int o = v0c + e;                         // output index of this pencil
+          if constexpr (pass == kSZ) {
+            // G[(v2, v1)][v0] with r = (v2, v1), o = v0
+            const df p = re * im;
+            float2* gp = G + size_t(o) * N * N + r;
+            df g = p;
+            if (!first_term) {
+              const float2 old = __ldcg(gp);
+              g = df{old.x, old.y} + p;
+            }
+            if (!last_term) {
+              __stcg(gp, make_float2(g.h, g.l));
+            } else {
+              // Q[v0][v1][v2]
+              Tio* qp = Q + (size_t(o) * N + (r % N)) * N + (r / N);
+              Tio out;
+              if constexpr (sizeof(Tio) == 8) out = Tio(df_to_double(g));
+              else out = Tio(__fadd_rn(g.h, g.l));
+              bad |= !::isfinite(double(out));
+              *qp = out;
+            }
+          } else if constexpr (pass == kSF0) {
+            const int k2h = r / N, k1 = r % N, k0 = o;
+            float4 v = make_float4(re.h, re.l, -im.h, -im.l);       // the forward transform conjugates
+            if (k0 == H || k1 == H) v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            lmax = fmaxf(lmax, __fadd_ru(fabsf(v.x), fabsf(v.z)));
+            Fs[(size_t(k0) * N + k1) * H + k2h] = v;
+          } else {
+            // next pass's row, slot = this pencil's next-K index:
+            //   F2: r = (v0, v1), out k2h -> row (k2h, v0), slot v1
+            //   F1: r = (k2h, v0), out k1 -> row (k2h, k1), slot v0
+            //   X:  r = (k0, k1), out v2 -> row (v2, k0), slot k1
+            //   Y:  r = (v2, k0), out v1 -> row (v2, v1), slot k0
+            constexpr int dstride = (pass == kSF2 || pass == kSX) ? N : 1;
+            const int drow0 = (pass == kSF2 || pass == kSX) ? r / N : (r / N) * N;
+            lmax = fmaxf(lmax, fmaxf(fabsf(re.h), fabsf(im.h)));
+            __stcg(buf + size_t(drow0 + o * dstride) * N + (r % N), make_float4(re.h, re.l, im.h, im.l));
+          }
+        }
+      }
+      fence_before();
+      wg_sync(wg);
+    }
+    if (next_max) atomic_max_nonneg(next_max, lmax);
+    return true;
+  }
+
+  // Whole cell; returns true (uniformly) if the CTA must stop (a wait expired).
+  static __device__ bool cell(const Tio* __restrict__ f, Tio* __restrict__ Q, const float4* __restrict__ tab,
+                              const float* __restrict__ tmax, int n_terms, unsigned char* ws, unsigned char* atile,
+                              uint32_t abase, uint32_t bbase, uint32_t tacc, uint32_t& phase, bool& pending,
+                              SlShared& sh, bool& bad) {
+    const int tid = threadIdx.x, wg = tid >> 7, lt = tid & 127;
+    float4* Fs = reinterpret_cast<float4*>(ws);
+    float4* buf = reinterpret_cast<float4*>(ws + C::F_BYTES);
+    float2* G = reinterpret_cast<float2*>(ws + C::F_BYTES + C::BUF_BYTES);
+    // barrier; zero the maximum slot that the next pass's epilogue writes; barrier
+    auto stop = [&](float* zero_slot) -> bool {
+      __syncthreads();
+      const bool v = *reinterpret_cast<volatile int*>(&sh.abort) != 0;
+      if (tid == 0 && zero_slot) *zero_slot = 0.0f;
+      __syncthreads();
+      return v;
+    };
+
+    float m = 0.0f;
+    for (int i = tid; i < N * N * N; i += C::THREADS) m = fmaxf(m, __double2float_ru(fabs(double(f[i]))));
+    if (tid == 0) { sh.pmax[0] = 0.0f; sh.pmax[1] = 0.0f; sh.Fmax = 0.0f; }
+    __syncthreads();
+    atomic_max_nonneg(&sh.pmax[0], m);
+    __syncthreads();
+    float si, so;
+    pass_scales(sh.pmax[0], &si, &so);
+    run<kSF2>(wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab, si, so, &sh.pmax[1],
+              false, false, bad);
+    if (stop(&sh.pmax[0])) return true;
+    pass_scales(sh.pmax[1], &si, &so);
+    run<kSF1>(wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab, si, so, &sh.pmax[0],
+              false, false, bad);
+    if (stop(&sh.pmax[1])) return true;
+    pass_scales(sh.pmax[0], &si, &so);
+    run<kSF0>(wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab, si, so, &sh.Fmax,
+              false, false, bad);
+    if (stop(nullptr)) return true;
+    const float Fmax = sh.Fmax;
+    for (int t = 0; t < n_terms; ++t) {
+      const float4* tab_t = tab + size_t(t) * N * N * H;
+      pass_scales(__fmul_ru(Fmax, tmax[t]), &si, &so);
+      run<kSX>(wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab_t, si, so,
+               &sh.pmax[1], false, false, bad);
+      if (stop(&sh.pmax[0])) return true;
+      pass_scales(sh.pmax[1], &si, &so);
+      run<kSY>(wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab_t, si, so,
+               &sh.pmax[0], false, false, bad);
+      if (stop(&sh.pmax[1])) return true;
+      pass_scales(sh.pmax[0], &si, &so);
+      run<kSZ>(wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab_t, si, so, nullptr,
+               t == 0, t == n_terms - 1, bad);
+      if (stop(nullptr)) return true;
+    }
+    return false;
+  }
+};
+
+template <int N, typename Tio>
+__global__ void __launch_bounds__(SlCfg<N>::THREADS, 1) sliced_kernel(CollArgs a) {
+  using C = SlCfg<N>;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  __shared__ SlShared sh;
+  const int tid = threadIdx.x, warp = tid >> 5, wg = tid >> 7;
+  const uint32_t raw = su32(smraw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* sm = smraw + (base - raw);
+  const uint32_t bbase = base;
+  const uint32_t abase = base + C::B_BYTES + wg * C::A_TILE;
+
+  // matrices: copy the pre-swizzled image
+  const unsigned char* img = static_cast<const unsigned char*>(a.tab) + sliced_img_offset(N, a.n_terms);
+  for (int i = tid; i < C::B_BYTES / 16; i += C::THREADS)
+    reinterpret_cast<uint4*>(sm)[i] = __ldg(reinterpret_cast<const uint4*>(img) + i);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&sh.tbase)),
+                 "r"(C::TCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int w = 0; w < C::WG; ++w)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&sh.bar[w])), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sh.abort = 0;
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tbase = sh.tbase;
+  const uint32_t tacc = tbase + wg * 3 * C::NOUT;
+  uint32_t phase = 0;
+  bool pending = false, bad = false;
+  const auto* tab = static_cast<const float4*>(a.tab);
+  const float* tmax = reinterpret_cast<const float*>(static_cast<const unsigned char*>(a.tab) +
+                                                     sliced_tmax_offset(N, a.n_terms));
+  unsigned char* ws = static_cast<unsigned char*>(a.ws) + size_t(blockIdx.x) * a.ws_per_cta;
+  for (long long c = blockIdx.x; c < a.n_cells; c += gridDim.x) {
+    const Tio* f = static_cast<const Tio*>(a.f) + size_t(c) * N * N * N;
+    Tio* Q = static_cast<Tio*>(a.Q) + size_t(c) * N * N * N;
+    if (SlCell<N, Tio>::cell(f, Q, tab, tmax, a.n_terms, ws, sm + C::B_BYTES + wg * C::A_TILE, abase, bbase, tacc,
+                             phase, pending, sh, bad))
+      break;
+  }
+  // a wait that expired may leave this warpgroup's last MMA batch in flight
+  if (pending) (void)wait_parity(&sh.bar[wg], phase);
+  fence_before();
+  if (__syncthreads_or(bad) && tid == 0) atomicOr(a.status, kStatusNonFinite);
+  if (sh.abort && tid == 0) atomicOr(a.status, kStatusTimeout);
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(C::TCOLS));
+  }
+}
+
+template <int N, typename Tio>
+int launch_sliced_t(const CollArgs& a, int grid, cudaStream_t st) {
+  using C = SlCfg<N>;
+  auto k = sliced_kernel<N, Tio>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  if (e != cudaSuccess) return int(e);
+  k<<<grid, C::THREADS, C::SMEM, st>>>(a);
+  return int(cudaGetLastError());
+}
+
+template <int N, typename Tio>
+int occupancy_sliced_t(int* ctas) {
+  using C = SlCfg<N>;
+  auto k = sliced_kernel<N, Tio>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  if (e != cudaSuccess) return int(e);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k, C::THREADS, C::SMEM);
+  const int by_tmem = 512 / C::TCOLS;
+  if (*ctas > by_tmem) *ctas = by_tmem;
+  return int(e);
+}
+
+uint16_t sl_half_bits(double x) {             // IEEE binary16, round to nearest even (host)
+  const __half h = __double2half(x);
+  uint16_t b;
+  std::memcpy(&b, &h, 2);
+  return b;
+}
+
+}  // namespace
+
+bool sliced_layout(int N, LayoutInfo* out) {
+  if (N != 16 && N != 32) return false;
+  LayoutInfo i;
+  i.N = N;
+  i.S0 = 1;
+  i.threads = N == 16 ? SlCfg<16>::THREADS : SlCfg<32>::THREADS;
+  i.fh_smem = false;
+  i.w_smem = false;
+  i.g_smem = false;
+  i.fh_bytes = N == 16 ? SlCfg<16>::F_BYTES : SlCfg<32>::F_BYTES;
+  i.w_bytes = N == 16 ? SlCfg<16>::BUF_BYTES : SlCfg<32>::BUF_BYTES;
+  i.g_bytes = N == 16 ? SlCfg<16>::G_BYTES : SlCfg<32>::G_BYTES;
+  *out = i;
+  return true;
+}
+
+int launch_sliced(int N, bool io_f64, const CollArgs& a, int grid, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (N == 16) return io_f64 ? launch_sliced_t<16, double>(a, grid, st) : launch_sliced_t<16, float>(a, grid, st);
+  if (N == 32) return io_f64 ? launch_sliced_t<32, double>(a, grid, st) : launch_sliced_t<32, float>(a, grid, st);
+  return int(cudaErrorInvalidValue);
+}
+
+int sliced_max_ctas_per_sm(int N, bool io_f64, int* ctas) {
+  if (N == 16) return io_f64 ? occupancy_sliced_t<16, double>(ctas) : occupancy_sliced_t<16, float>(ctas);
+  if (N == 32) return io_f64 ? occupancy_sliced_t<32, double>(ctas) : occupancy_sliced_t<32, float>(ctas);
+  return int(cudaErrorInvalidValue);
+}
+
+// Device image of a sliced plan: per-term tables [t][k0][k1][k2h] (A_h, A_l,
+// B_h, B_l) as float pairs, the per-term bound max|A + iB| (rounded up), then
+// the swizzled f16 matrices d0, d1, d2, dT, 2^-9 d1, 2^-9 d2 of the inverse
+// N-point DFT, one after another along K.
+coll_status build_sliced_image(const HostTables& ht, int N, std::vector<unsigned char>* out) {
+  if (N != 16 && N != 32) return COLL_EUNSUPPORTED;
+  const int H = N / 2, nt = ht.n_terms;
+  const int KP = 2 * N, NOUT = 2 * N;
+  const size_t img_off = sliced_img_offset(N, nt);
+  const size_t img_bytes = size_t(kSlMats * KP / 64) * NOUT * 128;
+  out->assign(img_off + img_bytes, 0);
+  float* tab = reinterpret_cast<float*>(out->data());
+  float* tmax = reinterpret_cast<float*>(out->data() + sliced_tmax_offset(N, nt));
+  for (int t = 0; t < nt; ++t) {
+    double mx = 0.0;
+    for (int k0 = 0; k0 < N; ++k0)
+      for (int k1 = 0; k1 < N; ++k1)
+        for (int k2 = 0; k2 < H; ++k2) {
+          const size_t src = ((size_t(t) * N + k0) * N + k1) * H + k2;
+          const double A = ht.tab[2 * src], B = ht.tab[2 * src + 1];
+          const float ah = float(A), bh = float(B);
+          tab[4 * src + 0] = ah;
+          tab[4 * src + 1] = float(A - double(ah));
+          tab[4 * src + 2] = bh;
+          tab[4 * src + 3] = float(B - double(bh));
+          mx = std::fmax(mx, std::sqrt(A * A + B * B));
+        }
+    tmax[t] = float(mx * (1.0 + 1e-6));
+  }
+  unsigned char* img = out->data() + img_off;
+  const double two_pi = 6.283185307179586476925286766559;
+  auto put = [&](int j, int kk, uint16_t val) {     // swizzled K-major position
+    const int kb = kk / 64, e = kk % 64, chunk = e / 8, within = e % 8;
+    const size_t off = size_t(kb) * NOUT * 128 + size_t(j) * 128 + size_t((chunk ^ (j & 7)) * 16) + size_t(within) * 2;
+    std::memcpy(img + off, &val, 2);
+  };
+  for (int j = 0; j < NOUT; ++j) {
+    const int v = j >> 1, ro = j & 1;
+    for (int kk = 0; kk < KP; ++kk) {
+      const int k = kk >> 1, ri = kk & 1;
+      const double th = two_pi * double((size_t(k) * v) % N) / double(N);
+      const double c = std::cos(th), sn = std::sin(th);
+      // [[cos, -sin], [sin, cos]] for y = sum e^{+i th} x
+      const double d = ro == 0 ? (ri == 0 ? c : -sn) : (ri == 0 ? sn : c);
+      // d = 2^-9 (d0 + 2^-9 d1 + 2^-18 (d2 + dT)), every step exact in double
+      const double t0 = d * 512.0, d0 = std::nearbyint(t0);
+      const double t1 = (t0 - d0) * 512.0, d1 = std::nearbyint(t1);
+      const double t2 = (t1 - d1) * 512.0, d2 = std::nearbyint(t2);
+      const double dT = t2 - d2;
+      const double m[kSlMats] = {d0, d1, d2, dT, d1 / 512.0, d2 / 512.0};
+      for (int s = 0; s < kSlMats; ++s) put(j, s * KP + kk, sl_half_bits(m[s]));
+    }
+  }
+  return COLL_OK;
+}
+
+}  // namespace coll
