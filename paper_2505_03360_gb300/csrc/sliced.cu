@@ -35,15 +35,16 @@
 // Layouts and row orders are those of mixed.cu.  A row of the A tile holds the
 // four parts one after another (K index 2N part + 2k + ri); the matrix image
 // holds d0, d1, d2, dT, 2^-9 d1, 2^-9 d2 one after another along K.  One CTA
-// per SM, persistent over cells; two warpgroups at N = 32 (shared memory:
-// 64 KB per A tile + 48 KB of matrices), four at N = 16; each warpgroup owns
-// three accumulators of 2N tensor-memory columns.  Every mbarrier wait is
+// per SM, persistent over cells, two warpgroups (shared memory at N = 32:
+// 64 KB per A tile + 48 KB of matrices); each warpgroup owns three
+// accumulators of 2N tensor-memory columns.  Every mbarrier wait is
 // bounded as in mixed.cu.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "coll_internal.h"
@@ -75,7 +76,7 @@ __host__ __device__ constexpr bool sl_pair_first(int i) { return i == 0 || i == 
 
 template <int N> struct SlCfg {
   static constexpr int H = N / 2;
-  static constexpr int WG = N == 16 ? 4 : 2;               // warpgroups per CTA (shared memory bound)
+  static constexpr int WG = 2;                             // warpgroups per CTA (shared memory bound at N = 32)
   static constexpr int THREADS = 128 * WG;
   static constexpr int KP = 2 * N;                         // f16 values per part per row
   static constexpr int KS = KP / 16;                       // 16-wide K steps per part
@@ -98,21 +99,40 @@ template <int N> struct SlCfg {
   static_assert(WG <= kSlMaxWG, "warpgroups");
 };
 
-// Parts of t = th + tl (a float pair, |t| < 2^9): s0, s1, s2 integers and the
-// tail sT, with t = s0 + 2^-9 s1 + 2^-18 (s2 + sT).  Every step but the last
-// addition is exact.
+// nearest integer (ties to even) of |x| <= 2^22, on the FMA pipe
+__device__ __forceinline__ float rint22(float x) { return __fsub_rn(__fadd_rn(x, 0x1.8p23f), 0x1.8p23f); }
+
+// Parts of t = th + tl (a float pair, |t| < 2^9, |tl| <= 2^-13): s0, s1, s2
+// integers and the tail sT, with t = s0 + 2^-9 s1 + 2^-18 (s2 + sT).  th has
+// 24 significant bits, so removing s0 and then 2^-9 s1 leaves an exact residual
+// b (a bit field of th, |b| <= 256 after the scaling by 2^18); tl enters at the
+// third level with one rounding (about 2^-43 of the pass maximum).
 __device__ __forceinline__ void slice4(float th, float tl, float (&s)[4]) {
-  const float s0 = rintf(th);
-  const df r = two_sum(__fsub_rn(th, s0), tl);
-  const float a = __fmul_rn(r.h, 512.0f), al = __fmul_rn(r.l, 512.0f);
-  const float s1 = rintf(a);
-  const df u = two_sum(__fsub_rn(a, s1), al);
-  const float b = __fmul_rn(u.h, 512.0f), bl = __fmul_rn(u.l, 512.0f);
-  const float s2 = rintf(b);
+  const float s0 = rint22(th);
+  const float a = __fmul_rn(__fsub_rn(th, s0), 512.0f);
+  const float s1 = rint22(a);
+  const float b = __fmul_rn(__fsub_rn(a, s1), 512.0f);
+  const float c = __fmaf_rn(tl, 262144.0f, b);
+  const float s2 = rint22(c);
   s[0] = s0;
   s[1] = s1;
   s[2] = s2;
-  s[3] = __fadd_rn(__fsub_rn(b, s2), bl);
+  s[3] = __fsub_rn(c, s2);
+}
+
+// a b + c d for float pairs: exact products of the heads, first-order cross
+// terms, one two-sum; the result is left unnormalised (tail below 2^-21 of the head)
+__device__ __forceinline__ df fma2(df a, df b, df c, df d) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  const float q = __fmul_rn(c.h, d.h);
+  float g = __fmaf_rn(c.h, d.h, -q);
+  g = __fmaf_rn(c.h, d.l, g);
+  g = __fmaf_rn(c.l, d.h, g);
+  const df t = two_sum(p, q);
+  return df{t.h, __fadd_rn(t.l, __fadd_rn(e, g))};
 }
 
 // value of one output component from the three level accumulators, times sc
@@ -122,8 +142,6 @@ __device__ __forceinline__ df combine(uint32_t u0, uint32_t u1, uint32_t u2, flo
   const df v = quick_two_sum(s.h, e);
   return df{__fmul_rn(v.h, sc), __fmul_rn(v.l, sc)};
 }
-
-__device__ __forceinline__ df dmul(df a, float s) { return df{__fmul_rn(a.h, s), __fmul_rn(a.l, s)}; }
 
 // scale of a pass from the maximum modulus m of its input: in = 2^(9-E), out = 2^(E-18)
 __device__ __forceinline__ void pass_scales(float m, float* in, float* out) {
@@ -161,86 +179,143 @@ struct SlCell {
     }
   }
 
-  // first forward pass: rows (v0, v1) of f, real values at slots v2
-  static __device__ __forceinline__ void stage_f(const Tio* __restrict__ f, int ti, int lt, unsigned char* atile,
-                                                 float sc) {
-    constexpr int RPI = 128 / N;                 // rows per sweep of the warpgroup
-    const int k = lt % N;
-#pragma unroll 4
-    for (int it = 0; it < N; ++it) {
-      const int row = it * RPI + lt / N;
-      const Tio x = f[size_t(ti * 128 + row) * N + k];
+  // Row of a 128-row tile staged by thread lt in sweep `it`, with LPR lanes per
+  // row: the rows of one warp instruction differ by 4, so that their stores fall
+  // on different 16-byte chunks of the 128-byte swizzle (no bank conflicts for
+  // LPR >= 16).
+  template <int LPR>
+  static __device__ __forceinline__ int stage_row(int it, int lt) {
+    return it * (128 / LPR) + (lt >> 5) + 4 * ((lt & 31) / LPR);
+  }
+
+  // Inputs of a tile are loaded into registers one chunk at a time: the first
+  // chunk of the next tile while the current tile's MMAs and epilogue run, each
+  // further chunk while the previous one is split into the A tile.  Passes F2
+  // (rows (v0, v1) of f, real values at slots v2) and F1, F0, Y, Z (rows of the
+  // pass buffer) take one slot per lane, N sweeps in chunks of 8; pass X takes
+  // H lanes per row, H sweeps in chunks of 2 (four loads per sweep).
+  static constexpr int BQ = 8;
+  static constexpr int XQ = 2;
+  struct PreF { Tio v[BQ]; };
+  struct PreBuf { float4 v[BQ]; };
+  struct PreX { float4 F[XQ], T[XQ], G[XQ], U[XQ]; };
+  static constexpr int chunks(int pass) { return pass == kSX ? H / XQ : N / BQ; }
+
+  static __device__ __forceinline__ void load(PreF& p, const Tio* __restrict__ f, const float4*, const float4*,
+                                              int ti, int lt, int c) {
+#pragma unroll
+    for (int i = 0; i < BQ; ++i)
+      p.v[i] = f[size_t(ti * 128 + stage_row<N>(c * BQ + i, lt)) * N + (lt & (N - 1))];
+  }
+  static __device__ __forceinline__ void put_chunk(const PreF& p, int lt, int c, unsigned char* atile, float sc) {
+#pragma unroll
+    for (int i = 0; i < BQ; ++i) {
       df v;
-      if constexpr (sizeof(Tio) == 8) v = df_from_double(double(x));
-      else v = df{float(x), 0.0f};
-      put(atile, row, k, __fmul_rn(v.h, sc), __fmul_rn(v.l, sc), 0.0f, 0.0f);
+      if constexpr (sizeof(Tio) == 8) v = df_from_double(double(p.v[i]));
+      else v = df{float(p.v[i]), 0.0f};
+      put(atile, stage_row<N>(c * BQ + i, lt), lt & (N - 1), __fmul_rn(v.h, sc), __fmul_rn(v.l, sc), 0.0f, 0.0f);
     }
   }
 
-  // passes F1, F0, Y, Z: 128 rows of the pass buffer, one complex slot per lane
-  static __device__ __forceinline__ void stage_buf(const float4* buf, int ti, int lt, unsigned char* atile,
-                                                   float sc) {
-    constexpr int RPI = 128 / N;
-    const int k = lt % N;
-#pragma unroll 4
-    for (int it = 0; it < N; ++it) {
-      const int row = it * RPI + lt / N;
-      const float4 v = __ldcg(buf + size_t(ti * 128 + row) * N + k);
-      put(atile, row, k, __fmul_rn(v.x, sc), __fmul_rn(v.y, sc), __fmul_rn(v.z, sc), __fmul_rn(v.w, sc));
+  static __device__ __forceinline__ void load(PreBuf& p, const Tio* __restrict__, const float4* buf, const float4*,
+                                              int ti, int lt, int c) {
+#pragma unroll
+    for (int i = 0; i < BQ; ++i)
+      p.v[i] = __ldcg(buf + size_t(ti * 128 + stage_row<N>(c * BQ + i, lt)) * N + (lt & (N - 1)));
+  }
+  static __device__ __forceinline__ void put_chunk(const PreBuf& p, int lt, int c, unsigned char* atile, float sc) {
+#pragma unroll
+    for (int i = 0; i < BQ; ++i) {
+      const float4 v = p.v[i];
+      put(atile, stage_row<N>(c * BQ + i, lt), lt & (N - 1), __fmul_rn(v.x, sc), __fmul_rn(v.y, sc),
+          __fmul_rn(v.z, sc), __fmul_rn(v.w, sc));
     }
   }
 
   // pass X: row (k0, k1), slot k2: (A + iB) F for k2 < N/2 from row (k0, k1) of F
   // and of the term table, for k2 > N/2 from the partner row (-k0, -k1) at
   // N - k2 (conjugated F; the multipliers are even); slot N/2 is zero
-  static __device__ __forceinline__ void stage_x(const float4* Fs, const float4* __restrict__ tab_t, int ti,
-                                                 int lt, unsigned char* atile, float sc) {
-    constexpr int RPI = 128 / H;
-    const int k2 = lt % H;
-#pragma unroll 2
-    for (int it = 0; it < H; ++it) {
-      const int row = it * RPI + lt / H;
-      const int rr = ti * 128 + row;
+  static __device__ __forceinline__ void load(PreX& p, const Tio* __restrict__, const float4* Fs,
+                                              const float4* __restrict__ tab_t, int ti, int lt, int c) {
+    const int k2 = lt & (H - 1);
+#pragma unroll
+    for (int i = 0; i < XQ; ++i) {
+      const int rr = ti * 128 + stage_row<H>(c * XQ + i, lt);
       const int k0 = rr / N, k1 = rr % N;
       const int rp = ((N - k0) % N) * N + (N - k1) % N;
-      const float4 F = __ldcg(Fs + size_t(rr) * H + k2), T = __ldg(tab_t + size_t(rr) * H + k2);
-      const float4 G = __ldcg(Fs + size_t(rp) * H + k2), U = __ldg(tab_t + size_t(rp) * H + k2);
+      p.F[i] = __ldcg(Fs + size_t(rr) * H + k2);
+      p.T[i] = __ldg(tab_t + size_t(rr) * H + k2);
+      p.G[i] = __ldcg(Fs + size_t(rp) * H + k2);
+      p.U[i] = __ldg(tab_t + size_t(rp) * H + k2);
+    }
+  }
+  static __device__ __forceinline__ void put_chunk(const PreX& p, int lt, int c, unsigned char* atile, float sc) {
+    const int k2 = lt & (H - 1);
+#pragma unroll
+    for (int i = 0; i < XQ; ++i) {
+      const int row = stage_row<H>(c * XQ + i, lt);
+      const float4 F = p.F[i], T = p.T[i], G = p.G[i], U = p.U[i];
       {
         const df A{T.x, T.y}, B{T.z, T.w}, Fr{F.x, F.y}, Fi{F.z, F.w};
-        const df zr = dmul(A * Fr - B * Fi, sc), zi = dmul(A * Fi + B * Fr, sc);
-        put(atile, row, k2, zr.h, zr.l, zi.h, zi.l);
+        const df zr = fma2(A, Fr, df{-B.h, -B.l}, Fi), zi = fma2(A, Fi, B, Fr);
+        put(atile, row, k2, __fmul_rn(zr.h, sc), __fmul_rn(zr.l, sc), __fmul_rn(zi.h, sc), __fmul_rn(zi.l, sc));
       }
       if (k2 > 0) {
         const df A{U.x, U.y}, B{U.z, U.w}, Gr{G.x, G.y}, Gi{G.z, G.w};
-        const df zr = dmul(A * Gr + B * Gi, sc), zi = dmul(B * Gr - A * Gi, sc);
-        put(atile, row, N - k2, zr.h, zr.l, zi.h, zi.l);
+        const df zr = fma2(A, Gr, B, Gi), zi = fma2(B, Gr, df{-A.h, -A.l}, Gi);
+        put(atile, row, N - k2, __fmul_rn(zr.h, sc), __fmul_rn(zr.l, sc), __fmul_rn(zi.h, sc), __fmul_rn(zi.l, sc));
       } else {
 #pragma unroll
-        for (int p = 0; p < kSlParts; ++p)
-          *reinterpret_cast<uint32_t*>(atile + a_off(row, p * C::PART_B + 4 * H)) = 0u;
+        for (int pp = 0; pp < kSlParts; ++pp)
+          *reinterpret_cast<uint32_t*>(atile + a_off(row, pp * C::PART_B + 4 * H)) = 0u;
       }
     }
   }
 
+  // the whole A tile from its first chunk `a` (already loaded); chunk c + 1
+  // loads while chunk c is split (a rolled loop over chunk pairs keeps the code
+  // small); `a` is consumed
+  template <int NC, class P>
+  static __device__ __forceinline__ void stage(P& a, const Tio* __restrict__ f, const float4* src,
+                                               const float4* __restrict__ tab_t, int ti, int lt,
+                                               unsigned char* atile, float sc) {
+    static_assert(NC % 2 == 0, "chunk pairs");
+    P b;
+#pragma unroll 1
+    for (int c = 0; c < NC; c += 2) {
+      load(b, f, src, tab_t, ti, lt, c + 1);
+      put_chunk(a, lt, c, atile, sc);
+      if (c + 2 < NC) load(a, f, src, tab_t, ti, lt, c + 2);
+      put_chunk(b, lt, c + 1, atile, sc);
+    }
+  }
+
   // One pass over this warpgroup's tiles.  Returns false (uniformly over the
-  // warpgroup) if an MMA wait expired; the expired phase stays pending.
-  template <int pass>
-  static __device__ __forceinline__ bool run(int wg, int lt, unsigned char* atile, uint32_t abase, uint32_t bbase,
-                                             uint32_t tacc, uint32_t& phase, bool& pending, SlShared& sh,
-                                             const Tio* __restrict__ f, Tio* __restrict__ Q, float4* Fs,
-                                             float4* buf, float2* G, const float4* __restrict__ tab_t, float sc_in,
-                                             float sc_out, float* next_max, bool first_term, bool last_term,
-                                             bool& bad) {
-    constexpr int rows = (pass == kSF1 || pass == kSF0) ? H * N : N * N;
-    constexpr int nout = pass == kSF2 ? N : C::NOUT;
+  // warpgroup) if an MMA wait expired; the expired phase stays pending.  `kind`
+  // selects the A-tile source (0: f, pass F2; 1: F and the term table, pass X;
+  // 2: the pass buffer, passes F1, F0, Y, Z, told apart at run time).
+  template <int kind>
+  static __device__ __forceinline__ bool run(int pass, int wg, int lt, unsigned char* atile, uint32_t abase,
+                                             uint32_t bbase, uint32_t tacc, uint32_t& phase, bool& pending,
+                                             SlShared& sh, const Tio* __restrict__ f, Tio* __restrict__ Q,
+                                             float4* Fs, float4* buf, float2* G, const float4* __restrict__ tab_t,
+                                             float sc_in, float sc_out, float* next_max, bool first_term,
+                                             bool last_term, bool& bad) {
+    const int rows = (pass == kSF1 || pass == kSF0) ? H * N : N * N;
+    constexpr int nout = kind == 0 ? N : C::NOUT;
     const int q = lt >> 5;
     float lmax = 0.0f;
+    using Pre = typename std::conditional<kind == 0, PreF,
+                                          typename std::conditional<kind == 1, PreX, PreBuf>::type>::type;
+    constexpr int NC = kind == 1 ? H / XQ : N / BQ;
+    // the X pass reads F (Fs) and the term table; the other passes read f or the pass buffer
+    const float4* src = kind == 1 ? Fs : buf;
+    Pre pre;
+    if (wg < rows / 128) load(pre, f, src, tab_t, wg, lt, 0);
     for (int ti = wg; ti < rows / 128; ti += kWG) {
       const int r = ti * 128 + lt;
       // ---- A tile
-      if constexpr (pass == kSF2) stage_f(f, ti, lt, atile, sc_in);
-      else if constexpr (pass == kSX) stage_x(Fs, tab_t, ti, lt, atile, sc_in);
-      else stage_buf(buf, ti, lt, atile, sc_in);
+      stage<NC>(pre, f, src, tab_t, ti, lt, atile, sc_in);
       fence_async_smem();
       wg_sync(wg);
       // ---- MMAs: ten products into three accumulators
@@ -261,6 +336,8 @@ struct SlCell {
         }
         mma_commit(&sh.bar[wg]);
       }
+      // the next tile's first chunk is in flight during the MMAs and the epilogue
+      if (ti + kWG < rows / 128) load(pre, f, src, tab_t, ti + kWG, lt, 0);
       if (!wg_all(wg, wait_parity(&sh.bar[wg], phase))) {
         if (lt == 0) atomicExch(&sh.abort, 1);
         pending = true;
@@ -270,7 +347,19 @@ struct SlCell {
       fence_after();
       // ---- epilogue: thread = TMEM lane = pencil row r
       const uint32_t lane_base = static_cast<uint32_t>(32 * q) << 16;
+      // pass Z: the gain accumulator of the chunk's 8 outputs, loaded one chunk ahead
+      float2 gcur[8], gnxt[8];
+      const bool zacc = kind == 2 && pass == kSZ && !first_term;
+      if (zacc) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) gcur[e] = __ldcg(G + size_t(e) * N * N + r);
+      }
+#pragma unroll 1
       for (int c0 = 0; c0 < nout; c0 += 16) {
+        if (zacc && c0 + 16 < nout) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) gnxt[e] = __ldcg(G + size_t((c0 + 16) / 2 + e) * N * N + r);
+        }
         uint32_t u0[16], u1[16], u2[16];
         tld16_nw(tacc + lane_base + c0, u0);
         tld16_nw(tacc + C::NOUT + lane_base + c0, u1);
@@ -284,15 +373,12 @@ struct SlCell {
           const df re = combine(u0[2 * e], u1[2 * e], u2[2 * e], sc_out);
           const df im = combine(u0[2 * e + 1], u1[2 * e + 1], u2[2 * e + 1], sc_out);
           const int o = v0c + e;                         // output index of this pencil
-          if constexpr (pass == kSZ) {
+          if (kind == 2 && pass == kSZ) {
             // G[(v2, v1)][v0] with r = (v2, v1), o = v0
             const df p = re * im;
             float2* gp = G + size_t(o) * N * N + r;
             df g = p;
-            if (!first_term) {
-              const float2 old = __ldcg(gp);
-              g = df{old.x, old.y} + p;
-            }
+            if (!first_term) g = df{gcur[e].x, gcur[e].y} + p;
             if (!last_term) {
               __stcg(gp, make_float2(g.h, g.l));
             } else {
@@ -304,7 +390,7 @@ struct SlCell {
               bad |= !::isfinite(double(out));
               *qp = out;
             }
-          } else if constexpr (pass == kSF0) {
+          } else if (kind == 2 && pass == kSF0) {
             const int k2h = r / N, k1 = r % N, k0 = o;
             float4 v = make_float4(re.h, re.l, -im.h, -im.l);       // the forward transform conjugates
             if (k0 == H || k1 == H) v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -316,11 +402,15 @@ struct SlCell {
             //   F1: r = (k2h, v0), out k1 -> row (k2h, k1), slot v0
             //   X:  r = (k0, k1), out v2 -> row (v2, k0), slot k1
             //   Y:  r = (v2, k0), out v1 -> row (v2, v1), slot k0
-            constexpr int dstride = (pass == kSF2 || pass == kSX) ? N : 1;
-            const int drow0 = (pass == kSF2 || pass == kSX) ? r / N : (r / N) * N;
+            const int dstride = kind != 2 ? N : 1;
+            const int drow0 = kind != 2 ? r / N : (r / N) * N;
             lmax = fmaxf(lmax, fmaxf(fabsf(re.h), fabsf(im.h)));
             __stcg(buf + size_t(drow0 + o * dstride) * N + (r % N), make_float4(re.h, re.l, im.h, im.l));
           }
+        }
+        if (zacc) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) gcur[e] = gnxt[e];
         }
       }
       fence_before();
@@ -356,30 +446,30 @@ struct SlCell {
     __syncthreads();
     float si, so;
     pass_scales(sh.pmax[0], &si, &so);
-    run<kSF2>(wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab, si, so, &sh.pmax[1],
+    run<0>(kSF2, wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab, si, so, &sh.pmax[1],
               false, false, bad);
     if (stop(&sh.pmax[0])) return true;
     pass_scales(sh.pmax[1], &si, &so);
-    run<kSF1>(wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab, si, so, &sh.pmax[0],
+    run<2>(kSF1, wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab, si, so, &sh.pmax[0],
               false, false, bad);
     if (stop(&sh.pmax[1])) return true;
     pass_scales(sh.pmax[0], &si, &so);
-    run<kSF0>(wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab, si, so, &sh.Fmax,
+    run<2>(kSF0, wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab, si, so, &sh.Fmax,
               false, false, bad);
     if (stop(nullptr)) return true;
     const float Fmax = sh.Fmax;
     for (int t = 0; t < n_terms; ++t) {
       const float4* tab_t = tab + size_t(t) * N * N * H;
       pass_scales(__fmul_ru(Fmax, tmax[t]), &si, &so);
-      run<kSX>(wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab_t, si, so,
+      run<1>(kSX, wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab_t, si, so,
                &sh.pmax[1], false, false, bad);
       if (stop(&sh.pmax[0])) return true;
       pass_scales(sh.pmax[1], &si, &so);
-      run<kSY>(wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab_t, si, so,
+      run<2>(kSY, wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab_t, si, so,
                &sh.pmax[0], false, false, bad);
       if (stop(&sh.pmax[1])) return true;
       pass_scales(sh.pmax[0], &si, &so);
-      run<kSZ>(wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab_t, si, so, nullptr,
+      run<2>(kSZ, wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab_t, si, so, nullptr,
                t == 0, t == n_terms - 1, bad);
       if (stop(nullptr)) return true;
     }
