@@ -20,10 +20,13 @@
 //     L2 = s0 d2 + s1 d1 + s2 d0 + s0 dT + sT d0 + 2^-9 (s1 d2 + s2 d1)
 // f16 x f16 products are exact in FP32, and every partial sum of L0 and of L1
 // is an integer below 2^24 in modulus (|s0| sum_k |d0| <= 512 (512 N sqrt 2 + N)
-// and the like), so the FP32 accumulators of L0 and L1 are exact; only L2
-// rounds, at about 2^-42 of L0's scale.  The products left out are below 2^-45
-// of it.  Each level has its own tensor-memory accumulator; the epilogue
-// combines them into a float pair (hi + lo, about 48 bits).
+// and the like), so the FP32 accumulators of L0 and of 2^-9 L1 (taken against
+// the matrices 2^-9 d1 and 2^-9 d0: multiples of 2^-9 below 2^15) are exact;
+// only L2 rounds, at about 2^-42 of L0's scale.  The products left out are
+// below 2^-45 of it.  Each level has its own tensor-memory accumulator; the
+// epilogue combines them into a normalised float pair (hi + lo, about 48 bits)
+// in units of the level-0 accumulator, and the next pass rescales by a power
+// of two.
 //
 // Intermediates: the forward spectrum F, the pass buffer and the gain
 // accumulator G are float pairs in the CTA's workspace (L2 resident), and the
@@ -34,11 +37,15 @@
 //
 // Layouts and row orders are those of mixed.cu.  A row of the A tile holds the
 // four parts one after another (K index 2N part + 2k + ri); the matrix image
-// holds d0, d1, d2, dT, 2^-9 d1, 2^-9 d2 one after another along K.  One CTA
-// per SM, persistent over cells, two warpgroups (shared memory at N = 32:
-// 64 KB per A tile + 48 KB of matrices); each warpgroup owns three
-// accumulators of 2N tensor-memory columns.  Every mbarrier wait is
-// bounded as in mixed.cu.
+// holds d0, d1, d2, dT, 2^-9 d1, 2^-9 d2, 2^-9 d0 one after another along K.
+// One cluster of two CTAs (two SMs) per cell, persistent over cells: the CTAs
+// split the tiles of every pass, meet at a cluster barrier between passes and
+// exchange the pass maxima through distributed shared memory, so the cell's
+// float-pair workspace (1 MB at N = 32) is shared by two SMs and the
+// workspaces of all resident cells stay in L2.  Two warpgroups per CTA
+// (shared memory at N = 32: 64 KB per A tile + 56 KB of matrices); each
+// warpgroup owns three accumulators of 2N tensor-memory columns.  Every
+// mbarrier wait is bounded as in mixed.cu.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -57,17 +64,18 @@ namespace {
 
 constexpr int kSlMaxWG = 4;
 constexpr int kSlParts = 4;      // s0, s1, s2, sT
-constexpr int kSlMats = 6;       // d0, d1, d2, dT, 2^-9 d1, 2^-9 d2
+constexpr int kSlMats = 7;       // d0, d1, d2, dT, 2^-9 d1, 2^-9 d2, 2^-9 d0
 constexpr int kSlPairs = 10;
 
-// A part and matrix of every product, in issue order: L0 = s0 d0; L1 = s0 d1 +
-// s1 d0; L2 = s0 d2 + s1 d1 + s2 d0 + s0 dT + sT d0 + s1 (2^-9 d2) + s2 (2^-9 d1)
+// A part and matrix of every product, in issue order: L0 = s0 d0;
+// 2^-9 L1 = s0 (2^-9 d1) + s1 (2^-9 d0) (multiples of 2^-9 below 2^15: still
+// exact); L2 = s0 d2 + s1 d1 + s2 d0 + s0 dT + sT d0 + s1 (2^-9 d2) + s2 (2^-9 d1)
 __host__ __device__ constexpr int sl_pair_a(int i) {
   constexpr int v[kSlPairs] = {0, 0, 1, 0, 1, 2, 0, 3, 1, 2};
   return v[i];
 }
 __host__ __device__ constexpr int sl_pair_b(int i) {
-  constexpr int v[kSlPairs] = {0, 1, 0, 2, 1, 0, 3, 0, 5, 4};
+  constexpr int v[kSlPairs] = {0, 4, 6, 2, 1, 0, 3, 0, 5, 4};
   return v[i];
 }
 __host__ __device__ constexpr int sl_pair_acc(int i) { return i == 0 ? 0 : (i < 3 ? 1 : 2); }
@@ -84,36 +92,41 @@ template <int N> struct SlCfg {
   static constexpr int KB = KROW / 64;                     // 128-byte K blocks per A row
   static constexpr int PART_B = 2 * KP;                    // bytes per part in an A row
   static constexpr int NOUT = 2 * N;                       // matrix rows (v, re/im)
-  static constexpr int B_BYTES = (kSlMats * KP / 64) * NOUT * 128;
+  static constexpr int BK = (kSlMats * KP + 63) / 64 * 64;  // K values of the matrix image (zero padded)
+  static constexpr int B_BYTES = (BK / 64) * NOUT * 128;
   static constexpr int A_TILE = KB * 128 * 128;
   static constexpr int TCOLS_USED = WG * 3 * NOUT;
   static constexpr int TCOLS = 512;
-  static constexpr int SMEM = B_BYTES + WG * A_TILE + 1024;
+  static constexpr int SMEM_USED = B_BYTES + WG * A_TILE + 1024;
+  // at least half an SM's shared memory, so that no two CTAs (each holding all
+  // 512 tensor-memory columns) ever share an SM: a second allocation would wait
+  // for the first CTA, which may itself wait at a cluster barrier
+  static constexpr int SMEM_MIN = 120 * 1024;
+  static constexpr int SMEM = SMEM_USED > SMEM_MIN ? SMEM_USED : SMEM_MIN;
   static constexpr size_t F_BYTES = size_t(N) * N * H * 16;        // half spectrum, complex float pairs
   static constexpr size_t BUF_BYTES = size_t(N) * N * N * 16;      // N^2 rows of N complex float pairs
   static constexpr size_t G_BYTES = size_t(N) * N * N * 8;         // gain accumulator, float pairs
-  static_assert(KROW % 64 == 0 && (kSlMats * KP) % 64 == 0, "K blocks");
+  static_assert(KROW % 64 == 0, "K blocks");
   static_assert(TCOLS_USED <= TCOLS, "tensor memory");
   static_assert(B_BYTES % 1024 == 0 && A_TILE % 1024 == 0, "1024-byte aligned tiles");
   static_assert(SMEM <= 232448, "shared memory");
   static_assert(WG <= kSlMaxWG, "warpgroups");
 };
 
-// nearest integer (ties to even) of |x| <= 2^22, on the FMA pipe
-__device__ __forceinline__ float rint22(float x) { return __fsub_rn(__fadd_rn(x, 0x1.8p23f), 0x1.8p23f); }
-
-// Parts of t = th + tl (a float pair, |t| < 2^9, |tl| <= 2^-13): s0, s1, s2
-// integers and the tail sT, with t = s0 + 2^-9 s1 + 2^-18 (s2 + sT).  th has
-// 24 significant bits, so removing s0 and then 2^-9 s1 leaves an exact residual
-// b (a bit field of th, |b| <= 256 after the scaling by 2^18); tl enters at the
-// third level with one rounding (about 2^-43 of the pass maximum).
-__device__ __forceinline__ void slice4(float th, float tl, float (&s)[4]) {
-  const float s0 = rint22(th);
-  const float a = __fmul_rn(__fsub_rn(th, s0), 512.0f);
-  const float s1 = rint22(a);
+// Parts of t = sc (th + tl) (sc a power of two, |t| < 2^9, |tl| <= ulp(th)):
+// s0, s1, s2 integers and the tail sT, with t = s0 + 2^-9 s1 + 2^-18 (s2 + sT).
+// th has 24 significant bits, so removing s0 and then 2^-9 s1 leaves an exact
+// residual b (a bit field of th, |b| <= 256 after the scaling by 2^18); tl
+// enters at the third level with one rounding (about 2^-43 of the pass
+// maximum); |s2| <= 257.
+__device__ __forceinline__ void slice4(float th, float tl, float sc, float (&s)[4]) {
+  constexpr float M = 0x1.8p23f;                         // rounds |x| <= 2^22 to an integer
+  const float s0 = __fsub_rn(__fmaf_rn(th, sc, M), M);
+  const float a = __fmul_rn(__fmaf_rn(th, sc, -s0), 512.0f);
+  const float s1 = __fsub_rn(__fadd_rn(a, M), M);
   const float b = __fmul_rn(__fsub_rn(a, s1), 512.0f);
-  const float c = __fmaf_rn(tl, 262144.0f, b);
-  const float s2 = rint22(c);
+  const float c = __fmaf_rn(tl, __fmul_rn(sc, 262144.0f), b);
+  const float s2 = __fsub_rn(__fadd_rn(c, M), M);
   s[0] = s0;
   s[1] = s1;
   s[2] = s2;
@@ -135,19 +148,25 @@ __device__ __forceinline__ df fma2(df a, df b, df c, df d) {
   return df{t.h, __fadd_rn(t.l, __fadd_rn(e, g))};
 }
 
-// value of one output component from the three level accumulators, times sc
-__device__ __forceinline__ df combine(uint32_t u0, uint32_t u1, uint32_t u2, float sc) {
-  const df s = two_sum(__uint_as_float(u0), __fmul_rn(__uint_as_float(u1), 0x1p-9f));
-  const float e = __fmaf_rn(__uint_as_float(u2), 0x1p-18f, s.l);
-  const df v = quick_two_sum(s.h, e);
-  return df{__fmul_rn(v.h, sc), __fmul_rn(v.l, sc)};
+// value of one output component, L0 + 2^-9 L1 + 2^-18 L2, in units of the
+// level-0 accumulator: an exact two-sum of the exact levels, the third level
+// added to the tail, then renormalised.  The renormalisation keeps the tail
+// below an ulp of the head; without it the tail of a small output would carry
+// the previous pass's scale, and the next slicing's third part would grow
+// from pass to pass past f16's exact integers.
+__device__ __forceinline__ df combine(uint32_t u0, uint32_t u1, uint32_t u2) {
+  const df s = two_sum(__uint_as_float(u0), __uint_as_float(u1));
+  return quick_two_sum(s.h, __fmaf_rn(__uint_as_float(u2), 0x1p-18f, s.l));
 }
 
-// scale of a pass from the maximum modulus m of its input: in = 2^(9-E), out = 2^(E-18)
-__device__ __forceinline__ void pass_scales(float m, float* in, float* out) {
+// Scales of a pass from the maximum modulus m of its input (in the unit of the
+// stored input, whose true size is `unit`): the input is multiplied by
+// in = 2^(9-E) before slicing (2^E > m), and one level-0 unit of the output is
+// worth unit 2^(E-18)
+__device__ __forceinline__ void pass_scales(float m, float unit, float* in, float* out_unit) {
   const int E = exp_of(__fmul_ru(m, 1.000001f));
   *in = ldexpf(1.0f, 9 - E);
-  *out = ldexpf(1.0f, E - 18);
+  *out_unit = __fmul_rn(unit, ldexpf(1.0f, E - 18));
 }
 
 enum SlPass : int { kSF2 = 0, kSF1, kSF0, kSX, kSY, kSZ };
@@ -155,10 +174,10 @@ enum SlPass : int { kSF2 = 0, kSF1, kSF0, kSX, kSY, kSZ };
 struct SlShared {
   uint64_t bar[kSlMaxWG];
   uint32_t tbase;
-  int abort;
-  float pmax[2];        // maximum modulus of the current / next pass input
-  float Fmax;           // max (|Re F| + |Im F|)
+  uint32_t abort;       // set in both CTAs of the cluster by a warpgroup whose wait expired
+  float mx[3];          // [0], [1]: maximum modulus of the current / next pass input; [2]: max (|Re F| + |Im F|)
 };
+constexpr int kSlotF = 2;
 
 template <int N, typename Tio>
 struct SlCell {
@@ -168,10 +187,10 @@ struct SlCell {
 
   // parts of the complex value (re, im) (scaled float pairs) into slot k of A-tile row `row`
   static __device__ __forceinline__ void put(unsigned char* atile, int row, int k, float rh, float rl, float ih,
-                                             float il) {
+                                             float il, float sc) {
     float a[4], b[4];
-    slice4(rh, rl, a);
-    slice4(ih, il, b);
+    slice4(rh, rl, sc, a);
+    slice4(ih, il, sc, b);
 #pragma unroll
     for (int p = 0; p < kSlParts; ++p) {
       const __half2 h = __floats2half2_rn(a[p], b[p]);
@@ -194,7 +213,7 @@ struct SlCell {
   // (rows (v0, v1) of f, real values at slots v2) and F1, F0, Y, Z (rows of the
   // pass buffer) take one slot per lane, N sweeps in chunks of 8; pass X takes
   // H lanes per row, H sweeps in chunks of 2 (four loads per sweep).
-  static constexpr int BQ = 8;
+  static constexpr int BQ = 4;
   static constexpr int XQ = 2;
   struct PreF { Tio v[BQ]; };
   struct PreBuf { float4 v[BQ]; };
@@ -213,7 +232,7 @@ struct SlCell {
       df v;
       if constexpr (sizeof(Tio) == 8) v = df_from_double(double(p.v[i]));
       else v = df{float(p.v[i]), 0.0f};
-      put(atile, stage_row<N>(c * BQ + i, lt), lt & (N - 1), __fmul_rn(v.h, sc), __fmul_rn(v.l, sc), 0.0f, 0.0f);
+      put(atile, stage_row<N>(c * BQ + i, lt), lt & (N - 1), v.h, v.l, 0.0f, 0.0f, sc);
     }
   }
 
@@ -227,8 +246,7 @@ struct SlCell {
 #pragma unroll
     for (int i = 0; i < BQ; ++i) {
       const float4 v = p.v[i];
-      put(atile, stage_row<N>(c * BQ + i, lt), lt & (N - 1), __fmul_rn(v.x, sc), __fmul_rn(v.y, sc),
-          __fmul_rn(v.z, sc), __fmul_rn(v.w, sc));
+      put(atile, stage_row<N>(c * BQ + i, lt), lt & (N - 1), v.x, v.y, v.z, v.w, sc);
     }
   }
 
@@ -258,12 +276,12 @@ struct SlCell {
       {
         const df A{T.x, T.y}, B{T.z, T.w}, Fr{F.x, F.y}, Fi{F.z, F.w};
         const df zr = fma2(A, Fr, df{-B.h, -B.l}, Fi), zi = fma2(A, Fi, B, Fr);
-        put(atile, row, k2, __fmul_rn(zr.h, sc), __fmul_rn(zr.l, sc), __fmul_rn(zi.h, sc), __fmul_rn(zi.l, sc));
+        put(atile, row, k2, zr.h, zr.l, zi.h, zi.l, sc);
       }
       if (k2 > 0) {
         const df A{U.x, U.y}, B{U.z, U.w}, Gr{G.x, G.y}, Gi{G.z, G.w};
         const df zr = fma2(A, Gr, B, Gi), zi = fma2(B, Gr, df{-A.h, -A.l}, Gi);
-        put(atile, row, N - k2, __fmul_rn(zr.h, sc), __fmul_rn(zr.l, sc), __fmul_rn(zi.h, sc), __fmul_rn(zi.l, sc));
+        put(atile, row, N - k2, zr.h, zr.l, zi.h, zi.l, sc);
       } else {
 #pragma unroll
         for (int pp = 0; pp < kSlParts; ++pp)
@@ -299,10 +317,14 @@ struct SlCell {
                                              uint32_t bbase, uint32_t tacc, uint32_t& phase, bool& pending,
                                              SlShared& sh, const Tio* __restrict__ f, Tio* __restrict__ Q,
                                              float4* Fs, float4* buf, float2* G, const float4* __restrict__ tab_t,
-                                             float sc_in, float sc_out, float* next_max, bool first_term,
+                                             float sc_in, float sc_out, int next_slot, bool first_term,
                                              bool last_term, bool& bad) {
     const int rows = (pass == kSF1 || pass == kSF0) ? H * N : N * N;
     constexpr int nout = kind == 0 ? N : C::NOUT;
+    const int crank = int(cluster_ctarank());          // the two CTAs of the cluster split the tiles
+    // F0 writes F and Z accumulates G in true units (times sc_out); the other
+    // passes store their outputs in level-0 units of the pass
+    const bool to_true = kind == 2 && (pass == kSF0 || pass == kSZ);
     const int q = lt >> 5;
     float lmax = 0.0f;
     using Pre = typename std::conditional<kind == 0, PreF,
@@ -311,8 +333,9 @@ struct SlCell {
     // the X pass reads F (Fs) and the term table; the other passes read f or the pass buffer
     const float4* src = kind == 1 ? Fs : buf;
     Pre pre;
-    if (wg < rows / 128) load(pre, f, src, tab_t, wg, lt, 0);
-    for (int ti = wg; ti < rows / 128; ti += kWG) {
+    const int ti0 = crank * kWG + wg;
+    if (ti0 < rows / 128) load(pre, f, src, tab_t, ti0, lt, 0);
+    for (int ti = ti0; ti < rows / 128; ti += 2 * kWG) {
       const int r = ti * 128 + lt;
       // ---- A tile
       stage<NC>(pre, f, src, tab_t, ti, lt, atile, sc_in);
@@ -337,9 +360,12 @@ struct SlCell {
         mma_commit(&sh.bar[wg]);
       }
       // the next tile's first chunk is in flight during the MMAs and the epilogue
-      if (ti + kWG < rows / 128) load(pre, f, src, tab_t, ti + kWG, lt, 0);
+      if (ti + 2 * kWG < rows / 128) load(pre, f, src, tab_t, ti + 2 * kWG, lt, 0);
       if (!wg_all(wg, wait_parity(&sh.bar[wg], phase))) {
-        if (lt == 0) atomicExch(&sh.abort, 1);
+        if (lt == 0) {
+          st_cluster_u32(cluster_addr(su32(&sh.abort), 0), 1u);
+          st_cluster_u32(cluster_addr(su32(&sh.abort), 1), 1u);
+        }
         pending = true;
         return false;
       }
@@ -370,8 +396,12 @@ struct SlCell {
         const int v0c = c0 >> 1;                         // first complex output of this chunk
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          const df re = combine(u0[2 * e], u1[2 * e], u2[2 * e], sc_out);
-          const df im = combine(u0[2 * e + 1], u1[2 * e + 1], u2[2 * e + 1], sc_out);
+          df re = combine(u0[2 * e], u1[2 * e], u2[2 * e]);
+          df im = combine(u0[2 * e + 1], u1[2 * e + 1], u2[2 * e + 1]);
+          if (to_true) {                                // passes F0 and Z: true units
+            re = df{__fmul_rn(re.h, sc_out), __fmul_rn(re.l, sc_out)};
+            im = df{__fmul_rn(im.h, sc_out), __fmul_rn(im.l, sc_out)};
+          }
           const int o = v0c + e;                         // output index of this pencil
           if (kind == 2 && pass == kSZ) {
             // G[(v2, v1)][v0] with r = (v2, v1), o = v0
@@ -416,7 +446,14 @@ struct SlCell {
       fence_before();
       wg_sync(wg);
     }
-    if (next_max) atomic_max_nonneg(next_max, lmax);
+    if (next_slot >= 0) {
+      // warp maximum, then into the slot of both CTAs of the cluster
+      const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(lmax));
+      if ((lt & 31) == 0) {
+        red_max_cluster(cluster_addr(su32(&sh.mx[next_slot]), 0), __uint_as_float(wm));
+        red_max_cluster(cluster_addr(su32(&sh.mx[next_slot]), 1), __uint_as_float(wm));
+      }
+    }
     return true;
   }
 
@@ -429,49 +466,56 @@ struct SlCell {
     float4* Fs = reinterpret_cast<float4*>(ws);
     float4* buf = reinterpret_cast<float4*>(ws + C::F_BYTES);
     float2* G = reinterpret_cast<float2*>(ws + C::F_BYTES + C::BUF_BYTES);
-    // barrier; zero the maximum slot that the next pass's epilogue writes; barrier
-    auto stop = [&](float* zero_slot) -> bool {
-      __syncthreads();
-      const bool v = *reinterpret_cast<volatile int*>(&sh.abort) != 0;
-      if (tid == 0 && zero_slot) *zero_slot = 0.0f;
-      __syncthreads();
+    const int crank = int(cluster_ctarank());
+    // cluster barrier; zero the maximum slot that the next pass's epilogue writes; cluster barrier
+    auto stop = [&](int zero_slot) -> bool {
+      cluster_sync();
+      const bool v = *reinterpret_cast<volatile uint32_t*>(&sh.abort) != 0u;
+      if (tid == 0 && zero_slot >= 0) sh.mx[zero_slot] = 0.0f;
+      cluster_sync();
       return v;
     };
 
+    if (tid == 0) { sh.mx[0] = 0.0f; sh.mx[1] = 0.0f; sh.mx[kSlotF] = 0.0f; }
+    cluster_sync();
     float m = 0.0f;
-    for (int i = tid; i < N * N * N; i += C::THREADS) m = fmaxf(m, __double2float_ru(fabs(double(f[i]))));
-    if (tid == 0) { sh.pmax[0] = 0.0f; sh.pmax[1] = 0.0f; sh.Fmax = 0.0f; }
-    __syncthreads();
-    atomic_max_nonneg(&sh.pmax[0], m);
-    __syncthreads();
-    float si, so;
-    pass_scales(sh.pmax[0], &si, &so);
-    run<0>(kSF2, wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab, si, so, &sh.pmax[1],
-              false, false, bad);
-    if (stop(&sh.pmax[0])) return true;
-    pass_scales(sh.pmax[1], &si, &so);
-    run<2>(kSF1, wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab, si, so, &sh.pmax[0],
-              false, false, bad);
-    if (stop(&sh.pmax[1])) return true;
-    pass_scales(sh.pmax[0], &si, &so);
-    run<2>(kSF0, wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab, si, so, &sh.Fmax,
-              false, false, bad);
-    if (stop(nullptr)) return true;
-    const float Fmax = sh.Fmax;
+    for (int i = crank * C::THREADS + tid; i < N * N * N; i += 2 * C::THREADS)
+      m = fmaxf(m, __double2float_ru(fabs(double(f[i]))));
+    const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+    if ((tid & 31) == 0) {
+      red_max_cluster(cluster_addr(su32(&sh.mx[0]), 0), __uint_as_float(wm));
+      red_max_cluster(cluster_addr(su32(&sh.mx[0]), 1), __uint_as_float(wm));
+    }
+    cluster_sync();
+    // si: input scale of a pass; u: true size of one unit of the stored pass input
+    float si, u = 1.0f;
+    pass_scales(sh.mx[0], 1.0f, &si, &u);
+    run<0>(kSF2, wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab, si, 1.0f, 1,
+           false, false, bad);
+    if (stop(0)) return true;
+    pass_scales(sh.mx[1], u, &si, &u);
+    run<2>(kSF1, wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab, si, 1.0f, 0,
+           false, false, bad);
+    if (stop(1)) return true;
+    pass_scales(sh.mx[0], u, &si, &u);
+    run<2>(kSF0, wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab, si, u, kSlotF,
+           false, false, bad);
+    if (stop(-1)) return true;
+    const float Fmax = sh.mx[kSlotF];
     for (int t = 0; t < n_terms; ++t) {
       const float4* tab_t = tab + size_t(t) * N * N * H;
-      pass_scales(__fmul_ru(Fmax, tmax[t]), &si, &so);
-      run<1>(kSX, wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab_t, si, so,
-               &sh.pmax[1], false, false, bad);
-      if (stop(&sh.pmax[0])) return true;
-      pass_scales(sh.pmax[1], &si, &so);
-      run<2>(kSY, wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab_t, si, so,
-               &sh.pmax[0], false, false, bad);
-      if (stop(&sh.pmax[1])) return true;
-      pass_scales(sh.pmax[0], &si, &so);
-      run<2>(kSZ, wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab_t, si, so, nullptr,
-               t == 0, t == n_terms - 1, bad);
-      if (stop(nullptr)) return true;
+      pass_scales(__fmul_ru(Fmax, tmax[t]), 1.0f, &si, &u);
+      run<1>(kSX, wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab_t, si, 1.0f, 1,
+             false, false, bad);
+      if (stop(0)) return true;
+      pass_scales(sh.mx[1], u, &si, &u);
+      run<2>(kSY, wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab_t, si, 1.0f, 0,
+             false, false, bad);
+      if (stop(1)) return true;
+      pass_scales(sh.mx[0], u, &si, &u);
+      run<2>(kSZ, wg, lt, atile, abase, bbase, tacc, phase, pending, sh, f, Q, Fs, buf, G, tab_t, si, u, -1,
+             t == 0, t == n_terms - 1, bad);
+      if (stop(-1)) return true;
     }
     return false;
   }
@@ -502,12 +546,13 @@ __global__ void __launch_bounds__(SlCfg<N>::THREADS, 1) sliced_kernel(CollArgs a
     for (int w = 0; w < C::WG; ++w)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&sh.bar[w])), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    sh.abort = 0;
+    sh.abort = 0u;
   }
   fence_async_smem();
   fence_before();
   __syncthreads();
   fence_after();
+  cluster_sync();                          // the peer CTA is running before any remote shared-memory access
   const uint32_t tbase = sh.tbase;
   const uint32_t tacc = tbase + wg * 3 * C::NOUT;
   uint32_t phase = 0;
@@ -515,8 +560,9 @@ __global__ void __launch_bounds__(SlCfg<N>::THREADS, 1) sliced_kernel(CollArgs a
   const auto* tab = static_cast<const float4*>(a.tab);
   const float* tmax = reinterpret_cast<const float*>(static_cast<const unsigned char*>(a.tab) +
                                                      sliced_tmax_offset(N, a.n_terms));
-  unsigned char* ws = static_cast<unsigned char*>(a.ws) + size_t(blockIdx.x) * a.ws_per_cta;
-  for (long long c = blockIdx.x; c < a.n_cells; c += gridDim.x) {
+  // a cell per cluster of two CTAs; the cluster works in the workspace slot of its first CTA
+  unsigned char* ws = static_cast<unsigned char*>(a.ws) + size_t(blockIdx.x & ~1u) * a.ws_per_cta;
+  for (long long c = blockIdx.x >> 1; c < a.n_cells; c += gridDim.x >> 1) {
     const Tio* f = static_cast<const Tio*>(a.f) + size_t(c) * N * N * N;
     Tio* Q = static_cast<Tio*>(a.Q) + size_t(c) * N * N * N;
     if (SlCell<N, Tio>::cell(f, Q, tab, tmax, a.n_terms, ws, sm + C::B_BYTES + wg * C::A_TILE, abase, bbase, tacc,
@@ -532,15 +578,40 @@ __global__ void __launch_bounds__(SlCfg<N>::THREADS, 1) sliced_kernel(CollArgs a
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(C::TCOLS));
   }
+  cluster_sync();                          // no CTA leaves while its peer may still address its shared memory
 }
 
+// Launch in clusters of two CTAs (one cell per cluster).  `grid` is the number
+// of CTAs the caller's workspace covers (a.ws_per_cta each); the kernel uses
+// every other slot, so any grid >= 1 fits: it runs max(1, grid / 2) clusters,
+// capped at the number of clusters that can be resident at once.
 template <int N, typename Tio>
 int launch_sliced_t(const CollArgs& a, int grid, cudaStream_t st) {
   using C = SlCfg<N>;
   auto k = sliced_kernel<N, Tio>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
   if (e != cudaSuccess) return int(e);
-  k<<<grid, C::THREADS, C::SMEM, st>>>(a);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(C::THREADS);
+  cfg.dynamicSmemBytes = C::SMEM;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  long long clusters = grid / 2 < 1 ? 1 : grid / 2;
+  if (clusters > a.n_cells) clusters = a.n_cells;
+  cfg.gridDim = dim3(2);
+  int resident = 0;
+  e = cudaOccupancyMaxActiveClusters(&resident, k, &cfg);
+  if (e != cudaSuccess) return int(e);
+  if (resident >= 1 && clusters > resident) clusters = resident;
+  cfg.gridDim = dim3(unsigned(2 * clusters));
+  e = cudaLaunchKernelEx(&cfg, k, a);
+  if (e != cudaSuccess) return int(e);
   return int(cudaGetLastError());
 }
 
@@ -596,14 +667,14 @@ int sliced_max_ctas_per_sm(int N, bool io_f64, int* ctas) {
 
 // Device image of a sliced plan: per-term tables [t][k0][k1][k2h] (A_h, A_l,
 // B_h, B_l) as float pairs, the per-term bound max|A + iB| (rounded up), then
-// the swizzled f16 matrices d0, d1, d2, dT, 2^-9 d1, 2^-9 d2 of the inverse
-// N-point DFT, one after another along K.
+// the swizzled f16 matrices d0, d1, d2, dT, 2^-9 d1, 2^-9 d2, 2^-9 d0 of the
+// inverse N-point DFT, one after another along K (zero padded to 64 values).
 coll_status build_sliced_image(const HostTables& ht, int N, std::vector<unsigned char>* out) {
   if (N != 16 && N != 32) return COLL_EUNSUPPORTED;
   const int H = N / 2, nt = ht.n_terms;
   const int KP = 2 * N, NOUT = 2 * N;
   const size_t img_off = sliced_img_offset(N, nt);
-  const size_t img_bytes = size_t(kSlMats * KP / 64) * NOUT * 128;
+  const size_t img_bytes = size_t((kSlMats * KP + 63) / 64) * NOUT * 128;
   out->assign(img_off + img_bytes, 0);
   float* tab = reinterpret_cast<float*>(out->data());
   float* tmax = reinterpret_cast<float*>(out->data() + sliced_tmax_offset(N, nt));
@@ -643,7 +714,7 @@ coll_status build_sliced_image(const HostTables& ht, int N, std::vector<unsigned
       const double t1 = (t0 - d0) * 512.0, d1 = std::nearbyint(t1);
       const double t2 = (t1 - d1) * 512.0, d2 = std::nearbyint(t2);
       const double dT = t2 - d2;
-      const double m[kSlMats] = {d0, d1, d2, dT, d1 / 512.0, d2 / 512.0};
+      const double m[kSlMats] = {d0, d1, d2, dT, d1 / 512.0, d2 / 512.0, d0 / 512.0};
       for (int s = 0; s < kSlMats; ++s) put(j, s * KP + kk, sl_half_bits(m[s]));
     }
   }

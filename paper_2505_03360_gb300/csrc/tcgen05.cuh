@@ -140,4 +140,28 @@ __device__ __forceinline__ void atomic_max_nonneg(float* a, float v) {
   atomicMax(reinterpret_cast<int*>(a), __float_as_int(v));   // non-negative floats order like their bits
 }
 
+// ---- thread-block clusters: rank, barrier, distributed shared memory
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// all threads of every CTA of the cluster; orders shared and global memory at cluster scope
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// shared::cluster address of the shared variable at CTA-local address saddr in CTA `rank`
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+// max of a non-negative float into a shared::cluster word (non-negative floats order like their bits)
+__device__ __forceinline__ void red_max_cluster(uint32_t caddr, float v) {
+  asm volatile("red.shared::cluster.max.u32 [%0], %1;" ::"r"(caddr), "r"(__float_as_uint(v)) : "memory");
+}
+__device__ __forceinline__ void st_cluster_u32(uint32_t caddr, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(caddr), "r"(v) : "memory");
+}
+
 }  // namespace coll
