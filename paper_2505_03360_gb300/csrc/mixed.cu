@@ -247,13 +247,17 @@ struct MixCell {
       if (lt == 0) {
         fence_after();
         const uint32_t id = idesc_f16(128, nout, S::kFmt);
+        // descriptors of the tile bases; each K step adds a compile-time offset
+        // to the 14-bit start-address field (shared addresses stay below 2^18
+        // bytes, so the field never carries)
+        const uint64_t ad = sw128_desc(abase), bd = sw128_desc(bbase);
         uint32_t acc = 0;
 #pragma unroll
         for (int sp = 0; sp < P; ++sp) {
 #pragma unroll
           for (int kk = 0; kk < (P - sp) * C::KP / 16; ++kk) {
-            mma_f16(tacc, sw128_desc(abase + (kk >> 2) * 16384 + (kk & 3) * 32),
-                    sw128_desc(bbase + C::set_off(sp) + (kk >> 2) * (C::NOUT * 128) + (kk & 3) * 32), id, acc);
+            mma_f16(tacc, ad + uint64_t(((kk >> 2) * 16384 + (kk & 3) * 32) >> 4),
+                    bd + uint64_t((C::set_off(sp) + (kk >> 2) * (C::NOUT * 128) + (kk & 3) * 32) >> 4), id, acc);
             acc = 1;
           }
         }

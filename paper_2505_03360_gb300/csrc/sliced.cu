@@ -345,6 +345,10 @@ struct SlCell {
       if (lt == 0) {
         fence_after();
         const uint32_t id = idesc_f16(128, nout, 0);
+        // descriptors of the tile bases; each K step adds a compile-time offset
+        // to the 14-bit start-address field (addresses stay below 2^18 bytes,
+        // so the field never carries)
+        const uint64_t ad = sw128_desc(abase), bd = sw128_desc(bbase);
 #pragma unroll
         for (int pi = 0; pi < kSlPairs; ++pi) {
           const int pa = sl_pair_a(pi), pb = sl_pair_b(pi), pc = sl_pair_acc(pi);
@@ -352,8 +356,8 @@ struct SlCell {
 #pragma unroll
           for (int j = 0; j < C::KS; ++j) {
             const int ka = pa * C::KS + j, kb = pb * C::KS + j;
-            mma_f16(tacc + pc * C::NOUT, sw128_desc(abase + (ka >> 2) * 16384 + (ka & 3) * 32),
-                    sw128_desc(bbase + (kb >> 2) * (C::NOUT * 128) + (kb & 3) * 32), id,
+            mma_f16(tacc + pc * C::NOUT, ad + uint64_t(((ka >> 2) * 16384 + (ka & 3) * 32) >> 4),
+                    bd + uint64_t(((kb >> 2) * (C::NOUT * 128) + (kb & 3) * 32) >> 4), id,
                     (first && j == 0) ? 0u : 1u);
           }
         }
