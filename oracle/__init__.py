@@ -16,6 +16,8 @@ Modules
   bkw         BKW exact solution for Maxwell molecules (closed-form pin)
   moments     moments, realizability matrices, L1 distance and mask bits
               (sec. 3.2, eq. for V_eps; App. A; sec. 3.3, L1 criterion)
+  regime      gradient indicators on the 2D grid (V_eps^1 eigenvalues,
+              lambda_B) and the regime update of Algorithm 1 (sec. 3.3, 4.5)
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 against closed forms, invariants, brute force or an independent formula.
