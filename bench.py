@@ -80,6 +80,31 @@ def sliced_mma_flops_per_cell(N: int, n_terms: int) -> float:
     return tiles_f2 * per(N) + tiles_full * per(2 * N)
 
 
+REGIME_FP64_OPS_PER_CELL = 126     # add/sub/mul/div/sqrt of the indicator sequence (4 div, 3 sqrt)
+REGIME_BYTES_PER_CELL = 4 * 8 + 8 + 1 + 1 + 4 * 8   # fields, l1, r in/out, indicators
+
+
+def time_regime(torch, coll, synth, dev, ny, nx, reps):
+    """Regime update (indicators + Algorithm 1) on an nx x ny grid: ms per launch (CUDA events)."""
+    dx = 1.0 / 256
+    F, r, l1 = synth.regime_fields(ny, nx, dx, synth.BASE_SEED + 6)
+    Fd, ld, rd = (torch.from_numpy(a).to(dev) for a in (F, l1, r))
+    out = torch.empty_like(rd)
+    ind = torch.empty((4, ny, nx), dtype=torch.float64, device=dev)
+    p = coll.coll_regime_params(1e-4, 1.0, 1.0, dx, dx, 1e-3, 2.8e-5, 1e-4)
+    st = torch.cuda.Stream(device=dev)
+    for _ in range(3):
+        coll.regime_update(Fd, ld, rd, nx, ny, p, out, ind, stream=st)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(reps):
+        coll.regime_update(Fd, ld, rd, nx, ny, p, out, ind, stream=st)
+    b.record(st)
+    torch.cuda.synchronize(dev)
+    return a.elapsed_time(b) / reps
+
+
 def max_over_ranks(x: float, world: int, device=None) -> float:
     """The slowest rank's value (the job's time); a no-op on one rank."""
     if world <= 1:
@@ -526,6 +551,20 @@ def run_ours(args, rank, world, local_rank):
                     "frac": (mom_bytes / (mom_ms / 1e3) / 1e9 / peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None,
                     "bytes_per_launch": mom_bytes, "bound": "hbm", "traffic": load_traffic("moments_f64")},
     }
+    # regime update on the 2D grid (indicators + Algorithm 1): the 256 x 256 spatial grid of
+    # the ragged workload, and a 4096 x 4096 grid (inputs > L2) for the throughput and roofline
+    t256 = time_regime(torch, coll, synth, dev, 256, 256, 50)
+    t4k = time_regime(torch, coll, synth, dev, 4096, 4096, 5)
+    c4k = 4096 * 4096
+    fp64_tf = REGIME_FP64_OPS_PER_CELL * c4k / (t4k / 1e3) / 1e12
+    line["regime"] = {
+        "kernel": "regime_kernel (central differences, V_eps^1 eigenvalues, lambda_B, Algorithm 1; FP64)",
+        "grid_256": {"ms_per_launch": t256, "cells_per_s": 65536 / (t256 / 1e3)},
+        "grid_4096": {"ms_per_launch": t4k, "cells_per_s": c4k / (t4k / 1e3)},
+        "roofline": {"bound": "alu", "achieved": fp64_tf, "peak": peak, "unit": "TFLOP/s", "frac": fp64_tf / peak,
+                     "peak_basis": "FP64 pipe (as the main line)",
+                     "flops_per_cell": REGIME_FP64_OPS_PER_CELL, "bytes_per_cell": REGIME_BYTES_PER_CELL,
+                     "hbm_gbs": REGIME_BYTES_PER_CELL * c4k / (t4k / 1e3) / 1e9}}
     if args.serve_requests > 0:
         from paper_2505_03360_gb300.service import Service, stream_jobs
         svc = Service(hbm_budget_bytes=120e9, device=str(dev))

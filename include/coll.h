@@ -245,6 +245,44 @@ coll_status moments_realizability(const void* f, int32_t io_dtype, int32_t N, do
                                   coll_moments* mom_out, uint8_t* mask_out, coll_stream stream);
 
 /*
+ * Regime update on the 2D spatial grid (sec. 4.5, Algorithm 1): per cell the
+ * central-difference gradients and Laplacians of rho, u_x, u_y, T over the
+ * one-cell stencil (sec. 4.5), the three eigenvalues of the 2D matrix
+ * V_eps^1 in closed form (sec. 3.3 and 4.5) with mu = mu0 sqrt(T) and
+ * kappa = kappa0 sqrt(T) (hard spheres, sec. 3.1), the indicator
+ * lambda_B = eps^2 (|grad T|^2/T + |grad u|^2
+ *                   + sqrt((|Delta u|^2 + |Delta rho/rho|^2)(1 + T^2))) (sec. 3.3),
+ * and the new regime:
+ *   r = 2: 2 if |lambda_B| > eta1, else 1
+ *   r = 1: 2 if |lambda_B| > eta1; else 0 if |lambda^k - 1| <= eta0 for all
+ *          three eigenvalues and l1 <= delta0; else 1
+ *   r = 0: 1 if |lambda^k - 1| > eta0 for some eigenvalue, else 0
+ * Delta u is the vector (Delta u_x, Delta u_y).
+ *   fields  device, 4 planes of (ny + 2) x (nx + 2) doubles, row-major
+ *           [q][j][i] with q = rho, u_x, u_y, T: the nx x ny cells and a
+ *           one-cell halo that the caller fills (boundary conditions)
+ *   l1      device, [ny][nx] doubles: ||f - M||_L1 of each cell (the l1 field
+ *           of moments_realizability); read only where r_in is 1
+ *   r_in    device, [ny][nx] regimes r^n in {0, 1, 2}
+ *   params  host: eps (Knudsen number), mu0, kappa0, dx, dy, eta0, eta1, delta0
+ *   r_out   device, [ny][nx] regimes r^{n+1}; may be r_in (each cell reads and
+ *           writes only its own entry).  A cell whose stencil holds a
+ *           non-finite value, with rho <= 0 or T <= 0, a regime above 2, or
+ *           (layer 1) a non-finite l1 keeps r^n with bit 7 set.
+ *   ind     device, [4][ny][nx] doubles lambda^a, lambda^b, lambda^c, lambda_B,
+ *           or NULL
+ * Every indicator is one fixed sequence of correctly rounded double
+ * operations, so r_out and ind are bitwise reproducible.  nx, ny >= 0
+ * (0 cells: no-op); COLL_EINVAL for null pointers, non-positive dx, dy or
+ * negative thresholds.  Asynchronous on stream.
+ */
+typedef struct {
+  double eps, mu0, kappa0, dx, dy, eta0, eta1, delta0;
+} coll_regime_params;
+coll_status regime_update(const double* fields, const double* l1, const uint8_t* r_in, int32_t nx, int32_t ny,
+                          const coll_regime_params* params, uint8_t* r_out, double* ind, coll_stream stream);
+
+/*
  * f <- f + dt * Q for n elements (io_dtype 0: double, 1: float), the explicit
  * Euler step of the space-homogeneous equation df/dt = Q(f,f) (sec. 2, the
  * kinetic equation without transport).  Device pointers, f and Q distinct;

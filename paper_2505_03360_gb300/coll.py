@@ -41,6 +41,10 @@ class coll_cell_group(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("f", ctypes.c_void_p), ("Q", ctypes.c_void_p)]
 
 
+class coll_regime_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("eps", "mu0", "kappa0", "dx", "dy", "eta0", "eta1", "delta0")]
+
+
 MOMENT_DOUBLES = 40
 
 
@@ -64,6 +68,7 @@ def _load():
                                              ctypes.POINTER(SZ)]),
         "coll_eval_ragged": (I32, [ctypes.POINTER(coll_cell_group), ctypes.POINTER(I64), I32, P, SZ, P]),
         "moments_realizability": (I32, [P, I32, I32, D, I64, D, D, P, P, P]),
+        "regime_update": (I32, [P, P, P, I32, I32, ctypes.POINTER(coll_regime_params), P, P, P]),
         "coll_device_status": (I32, [P]),
         "coll_device_status_clear": (I32, [P]),
         "coll_status_string": (ctypes.c_char_p, [I32]),
@@ -87,7 +92,8 @@ def header_functions() -> list:
     names = set()
     for h in HEADERS:
         txt = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
-        names.update(re.findall(r"^[A-Za-z_][\w\s\*]*?\b(coll_\w+|moments_realizability)\s*\(", txt, re.M))
+        names.update(re.findall(r"^[A-Za-z_][\w\s\*]*?\b(coll_\w+|moments_realizability|regime_update)\s*\(",
+                                txt, re.M))
     return sorted(names)
 
 
@@ -222,6 +228,27 @@ def moments_realizability(f, io_dtype: int, N: int, L: float, n_cells: int, eta0
     if check:
         _check(st, "moments_realizability")
     return st
+
+
+def regime_update(fields, l1, r_in, nx: int, ny: int, params: "coll_regime_params", r_out, ind=None, stream=None,
+                  check=True) -> int:
+    st = _lib.regime_update(_ptr(fields), _ptr(l1), _ptr(r_in), int(nx), int(ny), ctypes.byref(params), _ptr(r_out),
+                            _ptr(ind), _stream_ptr(stream))
+    if check:
+        _check(st, "regime_update")
+    return st
+
+
+def regime(fields, l1, r, eps, mu0, kappa0, dx, dy, eta0, eta1, delta0, indicators=False, stream=None):
+    """r^{n+1} [ny, nx] (uint8) and, if asked, the indicators [4, ny, nx] for
+    fields [4, ny + 2, nx + 2] (float64, with halo), l1 [ny, nx], r [ny, nx] on the device."""
+    import torch
+    ny, nx = r.shape
+    out = torch.empty_like(r)
+    ind = torch.empty((4, ny, nx), dtype=torch.float64, device=r.device) if indicators else None
+    p = coll_regime_params(eps, mu0, kappa0, dx, dy, eta0, eta1, delta0)
+    regime_update(fields, l1, r, nx, ny, p, out, ind, stream=stream)
+    return (out, ind) if indicators else out
 
 
 def coll_plan_tables_host(desc: coll_plan_desc):

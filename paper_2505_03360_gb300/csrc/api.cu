@@ -319,6 +319,21 @@ coll_status moments_realizability(const void* f, int32_t io_dtype, int32_t N, do
   return e == 0 ? COLL_OK : COLL_ECUDA;
 }
 
+coll_status regime_update(const double* fields, const double* l1, const uint8_t* r_in, int32_t nx, int32_t ny,
+                          const coll_regime_params* params, uint8_t* r_out, double* ind, coll_stream stream) {
+  if (nx < 0 || ny < 0 || !params) return COLL_EINVAL;
+  const coll_regime_params& p = *params;
+  if (!(p.dx > 0) || !(p.dy > 0) || !std::isfinite(p.dx) || !std::isfinite(p.dy) || !(p.eta0 >= 0) ||
+      !(p.eta1 >= 0) || !(p.delta0 >= 0) || !std::isfinite(p.eps) || !std::isfinite(p.mu0) ||
+      !std::isfinite(p.kappa0))
+    return COLL_EINVAL;
+  if (nx == 0 || ny == 0) return COLL_OK;
+  if (!fields || !l1 || !r_in || !r_out) return COLL_EINVAL;
+  count_launches(1);
+  const int e = launch_regime(fields, l1, r_in, nx, ny, p, r_out, ind, stream);
+  return e == 0 ? COLL_OK : COLL_ECUDA;
+}
+
 coll_status coll_device_status(coll_plan p) {
   if (!p) return COLL_EINVAL;
   int v = 0;

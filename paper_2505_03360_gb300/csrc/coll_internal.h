@@ -126,6 +126,10 @@ int sliced_max_ctas_per_sm(int N, bool io_f64, int* ctas);
 int launch_moments(const void* f, int io_f64, int N, double L, long long n_cells, double eta0,
                    double delta0, coll_moments* mom, uint8_t* mask, void* stream);
 
+// Regime update on the 2D grid (regime.cu)
+int launch_regime(const double* fields, const double* l1, const uint8_t* r_in, int nx, int ny,
+                  const coll_regime_params& p, uint8_t* r_out, double* ind, void* stream);
+
 // Host-side plan building (plan.cpp)
 struct HostTables {
   int n_terms;

@@ -235,3 +235,28 @@ def bimodal_batch_device(n_cells: int, N: int, L: float, seed: int, dtype=None, 
         out += (amp[:, None, None, None] * e[0][:, :, None, None] * e[1][:, None, :, None]
                 * e[2][:, None, None, :]).to(dtype)
     return out
+
+
+def regime_fields(ny: int, nx: int, dx: float, seed: int = BASE_SEED + 6):
+    """Macroscopic fields for the regime update on an nx x ny grid with a
+    one-cell halo: [4, ny + 2, nx + 2] float64 planes rho, u_x, u_y, T, each a
+    constant plus four seeded tanh(8 sin(k . x + phase)) bands (shock-like
+    fronts of random orientation); rho and T are kept >= 0.2.  Also a seeded
+    regime map r in {0, 1, 2} [ny, nx] (uint8) and an L1 distance map
+    10^U[-5, -3] [ny, nx] (spanning the paper's delta0 = 1e-4)."""
+    r = rng(seed)
+    y = (np.arange(ny + 2) - 0.5)[:, None] * dx
+    x = (np.arange(nx + 2) - 0.5)[None, :] * dx
+    out = []
+    for q, base in enumerate((1.0, 0.1, -0.2, 0.9)):
+        f = np.full((ny + 2, nx + 2), base)
+        for _ in range(4):
+            kx, ky, ph = r.uniform(1, 12), r.uniform(1, 12), r.uniform(0, 6.3)
+            f = f + (0.25 if q in (0, 3) else 0.6) * r.uniform(0.2, 1.0) * np.tanh(8 * np.sin(kx * x + ky * y + ph))
+        out.append(f)
+    F = np.stack(out)
+    F[0] = np.abs(F[0]) + 0.2
+    F[3] = np.abs(F[3]) + 0.2
+    regimes = r.integers(0, 3, (ny, nx)).astype(np.uint8)
+    l1 = 10.0 ** r.uniform(-5, -3, (ny, nx))
+    return F, regimes, l1
