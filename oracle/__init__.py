@@ -18,6 +18,8 @@ Modules
               (sec. 3.2, eq. for V_eps; App. A; sec. 3.3, L1 criterion)
   regime      gradient indicators on the 2D grid (V_eps^1 eigenvalues,
               lambda_B) and the regime update of Algorithm 1 (sec. 3.3, 4.5)
+  imex        penalised IMEX steps of df/dt = Q(f)/eps: eq. 1002 and the
+              PR(2,2,2) stages (sec. 4.3, 4.4)
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 against closed forms, invariants, brute force or an independent formula.
