@@ -565,6 +565,45 @@ def run_ours(args, rank, world, local_rank):
                      "peak_basis": "FP64 pipe (as the main line)",
                      "flops_per_cell": REGIME_FP64_OPS_PER_CELL, "bytes_per_cell": REGIME_BYTES_PER_CELL,
                      "hbm_gbs": REGIME_BYTES_PER_CELL * c4k / (t4k / 1e3) / 1e9}}
+    # penalised IMEX update (PR(2,2,2) stages, HBM-bound streams) on the same 4096 FP64 cells:
+    # the Y2 stage reads f, Y1 and Q(Y1) and writes Y2 (4 x 1.07 GB); then one whole PR(2,2,2)
+    # step (moments, 3 stages, 2 collision evaluations with the FP64 plan)
+    Y1 = torch.empty_like(f)
+    Y2 = torch.empty_like(f)
+    dt_, eps_ = 1e-2, 1.0
+    coll.coll_imex_stage(coll.IMEX_PR_Y1, f, None, None, None, None, mom, None, 0, N, w["L"], n, dt_, eps_, Y1,
+                         stream=stream)
+    for _ in range(3):
+        coll.coll_imex_stage(coll.IMEX_PR_Y2, f, Y1, Q, None, None, mom, None, 0, N, w["L"], n, dt_, eps_, Y2,
+                             stream=stream)
+    torch.cuda.synchronize(dev)
+    ia, ib = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ia.record(stream)
+    for _ in range(10):
+        coll.coll_imex_stage(coll.IMEX_PR_Y2, f, Y1, Q, None, None, mom, None, 0, N, w["L"], n, dt_, eps_, Y2,
+                             stream=stream)
+    ib.record(stream)
+    torch.cuda.synchronize(dev)
+    t_stage = ia.elapsed_time(ib) / 10
+    stage_bytes = 4 * f.numel() * 8
+    with torch.cuda.stream(stream):
+        coll.pr222_step(plan, f, w["L"], dt_, eps_, out=Y2, stream=stream)
+        torch.cuda.synchronize(dev)
+        pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        pa.record(stream)
+        coll.pr222_step(plan, f, w["L"], dt_, eps_, out=Y2, stream=stream)
+        pb.record(stream)
+    torch.cuda.synchronize(dev)
+    t_pr = pa.elapsed_time(pb)
+    del Y1, Y2
+    line["imex"] = {
+        "kernel": "imex_kernel (penalised IMEX stages, eq. 1002 / PR(2,2,2); FP64)",
+        "stage_y2_ms": t_stage, "stage_y2_bytes": stage_bytes,
+        "roofline": {"bound": "hbm", "achieved": stage_bytes / (t_stage / 1e3) / 1e9, "peak": peaks.get("hbm_gbs"),
+                     "unit": "GB/s",
+                     "frac": (stage_bytes / (t_stage / 1e3) / 1e9 / peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None},
+        "pr222_step_ms": t_pr,
+        "pr222_step": "moments + Y1 + Q(Y1) + Y2 + Q(Y2) + final on 4096 N=32 cells, FP64 collision plan"}
     if args.serve_requests > 0:
         from paper_2505_03360_gb300.service import Service, stream_jobs
         svc = Service(hbm_budget_bytes=120e9, device=str(dev))

@@ -283,6 +283,43 @@ coll_status regime_update(const double* fields, const double* l1, const uint8_t*
                           const coll_regime_params* params, uint8_t* r_out, double* ind, coll_stream stream);
 
 /*
+ * Penalised IMEX time stepping of the space-homogeneous Boltzmann equation
+ * df/dt = Q(f)/eps (sec. 4.4): Q is split as (Q - P) + P with the BGK-like
+ * P(f) = beta (M - f), beta = 2 pi rho, M the Maxwellian with the moments of
+ * f; Q - P is explicit, P implicit (solved in closed form because P keeps the
+ * moments).  One elementwise stage per call, for n_cells cells of N^3 values:
+ *   COLL_IMEX_FIRST_ORDER (eq. 1002): out = f^{n+1} from f, Q1 = Q(f) and
+ *       mom0 (moments of f); with a transport term tr = v . grad_x f (or NULL)
+ *       also mom1, the moments of f - dt tr (the U^{n+1} of the scheme):
+ *       out = eps/(eps + b1 dt) (f - dt tr) + dt (Q1 - b0 (M0 - f))/(eps + b1 dt)
+ *             + b1 dt/(eps + b1 dt) M1
+ *   COLL_IMEX_PR_Y1 .. COLL_IMEX_PR_FINAL: the stages of PR(2,2,2) (sec. 4.3
+ *       tableaux, g = 1 - 1/sqrt 2), all with the Maxwellian of f (mom0):
+ *       Y1 = (eps f + dt g b M) / (eps + dt g b)                  [f, mom0]
+ *       Y2 = (eps f + dt Q1 - 2 g dt b (M - Y) + dt g b M) / (eps + dt g b)
+ *                                                  [f, Y = Y1, Q1 = Q(Y1), mom0]
+ *       f^{n+1} = f + dt/(2 eps) (Q1 + Q2)          [f, Q1 = Q(Y1), Q2 = Q(Y2)]
+ *   One PR(2,2,2) step: moments_realizability(f), Y1, coll_eval_batch(Y1),
+ *   Y2, coll_eval_batch(Y2), final.
+ * All arrays are device pointers of io_dtype (0 double, 1 float) holding
+ * n_cells cells of N^3 values (N in {16, 24, 32, 48, 64}, other even N up to
+ * 64: COLL_EUNSUPPORTED); mom0 / mom1 are moments_realizability records.  Arrays a stage does not read may be NULL;
+ * out may be f (each value is read, then written, by the same thread).
+ * COLL_EINVAL for a missing array, eps <= 0, dt < 0 or a bad size.
+ * Asynchronous on stream; one launch.
+ */
+typedef enum {
+  COLL_IMEX_FIRST_ORDER = 0,
+  COLL_IMEX_PR_Y1 = 1,
+  COLL_IMEX_PR_Y2 = 2,
+  COLL_IMEX_PR_FINAL = 3
+} coll_imex_stage_kind;
+coll_status coll_imex_stage(int32_t stage, const void* f, const void* Y, const void* Q1, const void* Q2,
+                            const void* tr, const coll_moments* mom0, const coll_moments* mom1, int32_t io_dtype,
+                            int32_t N, double L, int64_t n_cells, double dt, double eps, void* out,
+                            coll_stream stream);
+
+/*
  * f <- f + dt * Q for n elements (io_dtype 0: double, 1: float), the explicit
  * Euler step of the space-homogeneous equation df/dt = Q(f,f) (sec. 2, the
  * kinetic equation without transport).  Device pointers, f and Q distinct;

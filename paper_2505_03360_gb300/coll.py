@@ -69,6 +69,7 @@ def _load():
         "coll_eval_ragged": (I32, [ctypes.POINTER(coll_cell_group), ctypes.POINTER(I64), I32, P, SZ, P]),
         "moments_realizability": (I32, [P, I32, I32, D, I64, D, D, P, P, P]),
         "regime_update": (I32, [P, P, P, I32, I32, ctypes.POINTER(coll_regime_params), P, P, P]),
+        "coll_imex_stage": (I32, [I32, P, P, P, P, P, P, P, I32, I32, D, I64, D, D, P, P]),
         "coll_device_status": (I32, [P]),
         "coll_device_status_clear": (I32, [P]),
         "coll_status_string": (ctypes.c_char_p, [I32]),
@@ -237,6 +238,37 @@ def regime_update(fields, l1, r_in, nx: int, ny: int, params: "coll_regime_param
     if check:
         _check(st, "regime_update")
     return st
+
+
+IMEX_FIRST_ORDER, IMEX_PR_Y1, IMEX_PR_Y2, IMEX_PR_FINAL = range(4)
+
+
+def coll_imex_stage(stage: int, f, Y, Q1, Q2, tr, mom0, mom1, io_dtype: int, N: int, L: float, n_cells: int,
+                    dt: float, eps: float, out, stream=None, check=True) -> int:
+    st = _lib.coll_imex_stage(int(stage), _ptr(f), _ptr(Y), _ptr(Q1), _ptr(Q2), _ptr(tr), _ptr(mom0), _ptr(mom1),
+                              int(io_dtype), int(N), float(L), int(n_cells), float(dt), float(eps), _ptr(out),
+                              _stream_ptr(stream))
+    if check:
+        _check(st, "coll_imex_stage")
+    return st
+
+
+def pr222_step(plan: "Plan", f, L: float, dt: float, eps: float, out=None, stream=None):
+    """One PR(2,2,2) step of df/dt = Q(f)/eps for f [n, N, N, N] on the device:
+    moments of f, Y1, Q(Y1), Y2, Q(Y2) through the plan, then the final stage."""
+    import torch
+    n, N = f.shape[0], f.shape[-1]
+    io = 0 if f.dtype == torch.float64 else 1
+    mom, _ = moments(f, L, stream=stream)
+    Y1 = torch.empty_like(f)
+    coll_imex_stage(IMEX_PR_Y1, f, None, None, None, None, mom, None, io, N, L, n, dt, eps, Y1, stream=stream)
+    Q1 = plan.eval(Y1, stream=stream)
+    Y2 = torch.empty_like(f)
+    coll_imex_stage(IMEX_PR_Y2, f, Y1, Q1, None, None, mom, None, io, N, L, n, dt, eps, Y2, stream=stream)
+    Q2 = plan.eval(Y2, stream=stream)
+    out = torch.empty_like(f) if out is None else out
+    coll_imex_stage(IMEX_PR_FINAL, f, None, Q1, Q2, None, None, None, io, N, L, n, dt, eps, out, stream=stream)
+    return out
 
 
 def regime(fields, l1, r, eps, mu0, kappa0, dx, dy, eta0, eta1, delta0, indicators=False, stream=None):

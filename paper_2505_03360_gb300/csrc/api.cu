@@ -334,6 +334,36 @@ coll_status regime_update(const double* fields, const double* l1, const uint8_t*
   return e == 0 ? COLL_OK : COLL_ECUDA;
 }
 
+coll_status coll_imex_stage(int32_t stage, const void* f, const void* Y, const void* Q1, const void* Q2,
+                            const void* tr, const coll_moments* mom0, const coll_moments* mom1, int32_t io_dtype,
+                            int32_t N, double L, int64_t n_cells, double dt, double eps, void* out,
+                            coll_stream stream) {
+  if (stage < COLL_IMEX_FIRST_ORDER || stage > COLL_IMEX_PR_FINAL || n_cells < 0) return COLL_EINVAL;
+  if ((io_dtype != 0 && io_dtype != 1) || !(N >= 2 && N <= 64 && N % 2 == 0)) return COLL_EINVAL;
+  if (N != 16 && N != 24 && N != 32 && N != 48 && N != 64) return COLL_EUNSUPPORTED;
+  if (!(eps > 0) || !std::isfinite(eps) || !(dt >= 0) || !std::isfinite(dt) || !(L > 0) || !std::isfinite(L))
+    return COLL_EINVAL;
+  if (n_cells == 0) return COLL_OK;
+  if (!f || !out) return COLL_EINVAL;
+  switch (stage) {
+    case COLL_IMEX_FIRST_ORDER:
+      if (!Q1 || !mom0 || (tr && !mom1)) return COLL_EINVAL;
+      break;
+    case COLL_IMEX_PR_Y1:
+      if (!mom0) return COLL_EINVAL;
+      break;
+    case COLL_IMEX_PR_Y2:
+      if (!Y || !Q1 || !mom0) return COLL_EINVAL;
+      break;
+    default:
+      if (!Q1 || !Q2) return COLL_EINVAL;
+  }
+  count_launches(1);
+  const int e = launch_imex(stage, f, Y, Q1, Q2, stage == COLL_IMEX_FIRST_ORDER ? tr : nullptr, mom0, mom1,
+                            io_dtype == 0, N, L, n_cells, dt, eps, out, stream);
+  return e == 0 ? COLL_OK : COLL_ECUDA;
+}
+
 coll_status coll_device_status(coll_plan p) {
   if (!p) return COLL_EINVAL;
   int v = 0;

@@ -130,6 +130,11 @@ int launch_moments(const void* f, int io_f64, int N, double L, long long n_cells
 int launch_regime(const double* fields, const double* l1, const uint8_t* r_in, int nx, int ny,
                   const coll_regime_params& p, uint8_t* r_out, double* ind, void* stream);
 
+// Penalised IMEX stages (imex.cu)
+int launch_imex(int stage, const void* f, const void* Y, const void* Q1, const void* Q2, const void* tr,
+                const coll_moments* mom0, const coll_moments* mom1, bool io_f64, int N, double L, long long n_cells,
+                double dt, double eps, void* out, void* stream);
+
 // Host-side plan building (plan.cpp)
 struct HostTables {
   int n_terms;
