@@ -20,6 +20,8 @@ Modules
               lambda_B) and the regime update of Algorithm 1 (sec. 3.3, 4.5)
   imex        penalised IMEX steps of df/dt = Q(f)/eps: eq. 1002 and the
               PR(2,2,2) stages (sec. 4.3, 4.4)
+  esbgk       ES-BGK Gaussian and operator (sec. 2.2) and its first-order
+              IMEX step (sec. 4.3, eq. 1000)
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 against closed forms, invariants, brute force or an independent formula.
