@@ -80,6 +80,9 @@ def sliced_mma_flops_per_cell(N: int, n_terms: int) -> float:
     return tiles_f2 * per(N) + tiles_full * per(2 * N)
 
 
+# the Gaussian's exponent (quadratic form, shared along a row), its exponential and the
+# step's combination, per value of f
+ESBGK_FP64_OPS_PER_VALUE = 11
 REGIME_FP64_OPS_PER_CELL = 126     # add/sub/mul/div/sqrt of the indicator sequence (4 div, 3 sqrt)
 REGIME_BYTES_PER_CELL = 4 * 8 + 8 + 1 + 1 + 4 * 8   # fields, l1, r in/out, indicators
 
@@ -604,6 +607,25 @@ def run_ours(args, rank, world, local_rank):
                      "frac": (stage_bytes / (t_stage / 1e3) / 1e9 / peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None},
         "pr222_step_ms": t_pr,
         "pr222_step": "moments + Y1 + Q(Y1) + Y2 + Q(Y2) + final on 4096 N=32 cells, FP64 collision plan"}
+    # ES-BGK relaxation step (layer 1) on the same 4096 FP64 cells: reads f and writes f^{n+1}
+    for _ in range(3):
+        coll.coll_esbgk_step(f, mom, 0, N, w["L"], n, 1e-2, 1.0, -0.5, 1.0, Q, stream=stream)
+    torch.cuda.synchronize(dev)
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    for _ in range(10):
+        coll.coll_esbgk_step(f, mom, 0, N, w["L"], n, 1e-2, 1.0, -0.5, 1.0, Q, stream=stream)
+    eb.record(stream)
+    torch.cuda.synchronize(dev)
+    t_es = ea.elapsed_time(eb) / 10
+    es_bytes = 2 * f.numel() * 8
+    es_tf = ESBGK_FP64_OPS_PER_VALUE * f.numel() / (t_es / 1e3) / 1e12
+    line["esbgk"] = {
+        "kernel": "esbgk_kernel (ES-BGK IMEX relaxation step, eq. 1000; FP64, beta = -1/2)",
+        "ms_per_launch": t_es, "cell_steps_per_s": n / (t_es / 1e3),
+        "roofline": {"bound": "alu", "achieved": es_tf, "peak": peak, "unit": "TFLOP/s", "frac": es_tf / peak,
+                     "peak_basis": "FP64 pipe (as the main line)", "flops_per_value": ESBGK_FP64_OPS_PER_VALUE,
+                     "hbm_gbs": es_bytes / (t_es / 1e3) / 1e9, "bytes_per_launch": es_bytes}}
     if args.serve_requests > 0:
         from paper_2505_03360_gb300.service import Service, stream_jobs
         svc = Service(hbm_budget_bytes=120e9, device=str(dev))

@@ -320,6 +320,25 @@ coll_status coll_imex_stage(int32_t stage, const void* f, const void* Y, const v
                             coll_stream stream);
 
 /*
+ * ES-BGK relaxation step (layer 1 of the hierarchy): one first-order IMEX step
+ * of the space-homogeneous equation df/dt = Q_ES(f)/eps (sec. 4.3, eq. 1000
+ * and the closed form after it) with Q_ES(f) = nu (G[f] - f), the Gaussian
+ * G[f] = rho / sqrt(det(2 pi Tau)) exp(-(v - u)^T Tau^{-1} (v - u) / 2) and
+ * the corrected tensor Tau = (1 - beta) T I + beta Theta (sec. 2.2,
+ * Pr = 1/(1 - beta); beta = -1/2 for hard spheres).  Per cell, from its
+ * moments record (rho, u, T, Theta of f^n): nu = rho sqrt(T)/((1 - beta) mu0),
+ *   Theta^{n+1} = (eps Theta + (1 - beta) nu dt T I)/(eps + (1 - beta) nu dt),
+ *   out = eps/(eps + nu dt) f + nu dt/(eps + nu dt) G[rho, u, Tau^{n+1}].
+ * f, out: device, n_cells cells of N^3 values of io_dtype (0 double, 1 float),
+ * N in {16, 24, 32, 48, 64}; mom: device records of moments_realizability for
+ * f.  out may be f.  COLL_EINVAL for eps <= 0, dt < 0, beta >= 1, mu0 <= 0 or
+ * a missing pointer.  Asynchronous on stream; one launch.
+ */
+coll_status coll_esbgk_step(const void* f, const coll_moments* mom, int32_t io_dtype, int32_t N, double L,
+                            int64_t n_cells, double dt, double eps, double beta, double mu0, void* out,
+                            coll_stream stream);
+
+/*
  * f <- f + dt * Q for n elements (io_dtype 0: double, 1: float), the explicit
  * Euler step of the space-homogeneous equation df/dt = Q(f,f) (sec. 2, the
  * kinetic equation without transport).  Device pointers, f and Q distinct;

@@ -70,6 +70,7 @@ def _load():
         "moments_realizability": (I32, [P, I32, I32, D, I64, D, D, P, P, P]),
         "regime_update": (I32, [P, P, P, I32, I32, ctypes.POINTER(coll_regime_params), P, P, P]),
         "coll_imex_stage": (I32, [I32, P, P, P, P, P, P, P, I32, I32, D, I64, D, D, P, P]),
+        "coll_esbgk_step": (I32, [P, P, I32, I32, D, I64, D, D, D, D, P, P]),
         "coll_device_status": (I32, [P]),
         "coll_device_status_clear": (I32, [P]),
         "coll_status_string": (ctypes.c_char_p, [I32]),
@@ -251,6 +252,25 @@ def coll_imex_stage(stage: int, f, Y, Q1, Q2, tr, mom0, mom1, io_dtype: int, N: 
     if check:
         _check(st, "coll_imex_stage")
     return st
+
+
+def coll_esbgk_step(f, mom, io_dtype: int, N: int, L: float, n_cells: int, dt: float, eps: float, beta: float,
+                    mu0: float, out, stream=None, check=True) -> int:
+    st = _lib.coll_esbgk_step(_ptr(f), _ptr(mom), int(io_dtype), int(N), float(L), int(n_cells), float(dt),
+                              float(eps), float(beta), float(mu0), _ptr(out), _stream_ptr(stream))
+    if check:
+        _check(st, "coll_esbgk_step")
+    return st
+
+
+def esbgk_step(f, L: float, dt: float, eps: float, beta: float = -0.5, mu0: float = 1.0, out=None, stream=None):
+    """One ES-BGK IMEX step of f [n, N, N, N] on the device (moments, then the relaxation)."""
+    import torch
+    n, N = f.shape[0], f.shape[-1]
+    mom, _ = moments(f, L, stream=stream)
+    out = torch.empty_like(f) if out is None else out
+    coll_esbgk_step(f, mom, 0 if f.dtype == torch.float64 else 1, N, L, n, dt, eps, beta, mu0, out, stream=stream)
+    return out
 
 
 def pr222_step(plan: "Plan", f, L: float, dt: float, eps: float, out=None, stream=None):

@@ -364,6 +364,22 @@ coll_status coll_imex_stage(int32_t stage, const void* f, const void* Y, const v
   return e == 0 ? COLL_OK : COLL_ECUDA;
 }
 
+coll_status coll_esbgk_step(const void* f, const coll_moments* mom, int32_t io_dtype, int32_t N, double L,
+                            int64_t n_cells, double dt, double eps, double beta, double mu0, void* out,
+                            coll_stream stream) {
+  if (n_cells < 0 || (io_dtype != 0 && io_dtype != 1)) return COLL_EINVAL;
+  if (!(N >= 2 && N <= 64 && N % 2 == 0)) return COLL_EINVAL;
+  if (N != 16 && N != 24 && N != 32 && N != 48 && N != 64) return COLL_EUNSUPPORTED;
+  if (!(eps > 0) || !std::isfinite(eps) || !(dt >= 0) || !std::isfinite(dt) || !(beta < 1) || !std::isfinite(beta) ||
+      !(mu0 > 0) || !std::isfinite(mu0) || !(L > 0) || !std::isfinite(L))
+    return COLL_EINVAL;
+  if (n_cells == 0) return COLL_OK;
+  if (!f || !mom || !out) return COLL_EINVAL;
+  count_launches(1);
+  const int e = launch_esbgk(f, mom, io_dtype == 0, N, L, n_cells, dt, eps, beta, mu0, out, stream);
+  return e == 0 ? COLL_OK : COLL_ECUDA;
+}
+
 coll_status coll_device_status(coll_plan p) {
   if (!p) return COLL_EINVAL;
   int v = 0;

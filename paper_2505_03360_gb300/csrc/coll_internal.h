@@ -135,6 +135,10 @@ int launch_imex(int stage, const void* f, const void* Y, const void* Q1, const v
                 const coll_moments* mom0, const coll_moments* mom1, bool io_f64, int N, double L, long long n_cells,
                 double dt, double eps, void* out, void* stream);
 
+// ES-BGK relaxation step (esbgk.cu)
+int launch_esbgk(const void* f, const coll_moments* mom, bool io_f64, int N, double L, long long n_cells, double dt,
+                 double eps, double beta, double mu0, void* out, void* stream);
+
 // Host-side plan building (plan.cpp)
 struct HostTables {
   int n_terms;
