@@ -22,6 +22,8 @@ Modules
               PR(2,2,2) stages (sec. 4.3, 4.4)
   esbgk       ES-BGK Gaussian and operator (sec. 2.2) and its first-order
               IMEX step (sec. 4.3, eq. 1000)
+  maxwell2d   fast spectral operator for 2D Maxwell molecules (sec. 4.4.1,
+              "The 2d case"), its O(N^4) spectral sum and the 2D BKW solution
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 against closed forms, invariants, brute force or an independent formula.
