@@ -339,6 +339,56 @@ coll_status coll_esbgk_step(const void* f, const coll_moments* mom, int32_t io_d
                             coll_stream stream);
 
 /*
+ * Two-dimensional Maxwell molecules (sec. 4.4.1, "The 2d case"): the fast
+ * spectral operator on a periodic 2D velocity grid, where the Carleman
+ * weight is the constant Bt = 2 b0 (collision kernel B = b0) and the
+ * separated kernel is exact up to the angle rule:
+ *   K(l, m) = Bt int_0^pi phi(xi_l . e_theta) phi(xi_m . e_theta^perp) dtheta
+ *          ~ sum_{p=1..A} c alpha_p(xi_l) alpha'_p(xi_m),
+ *   alpha_p(xi) = phi(xi . e_p), alpha'_p(xi) = phi(xi . e_p^perp),
+ *   phi(s) = 2R sinc(R s), theta_p = p pi / A, c = Bt pi / A,
+ * and Q = sum_p c IDFT(alpha_p fh) IDFT(alpha'_p fh) - IDFT(fh) IDFT(Lambda fh)
+ * with Lambda = sum_p c alpha_p alpha'_p and every |k_d| = N/2 mode dropped.
+ * A cell is N^2 contiguous values f[j0][j1] = f(v_{j0}, v_{j1}),
+ * v_j = -L + j 2L/N; cells are contiguous.
+ *
+ * Descriptor:
+ *   N        points per velocity axis: 16, 32 (COLL_F32 also 64)
+ *   L        half-width of the periodic box [-L, L)^2
+ *   S        support radius; truncation R = 2S; 0 selects 2L / (3 + sqrt 2)
+ *   b0       kernel constant; <= 0 selects 1/(2 pi) (int b dsigma = 1, the
+ *            BKW normalisation)
+ *   A        number of angles theta_p, 1 .. 4096
+ *   prec     COLL_F64, COLL_F32 or COLL_F32X2 (others: COLL_EUNSUPPORTED)
+ *   io_dtype 0: f and Q are double; 1: float
+ * coll_m2d_plan_create builds the table of (A_t, B_t) = (c alpha_p / N^2,
+ * alpha'_p / N^2) and the loss pair (-Lambda / N^2, 1 / N^2) on the half
+ * spectrum and uploads it to the current device (A + 1 terms); the plan owns
+ * it until coll_m2d_plan_destroy (synchronise first).  coll_m2d_eval_batch
+ * computes Q[c] for n_cells cells of f (device arrays of the plan's io type,
+ * Q not aliasing f) in one launch on stream, with no workspace: every
+ * intermediate stays in shared memory.  n_cells = 0 is a no-op.  Errors as
+ * for the 3D plan; non-finite results set the plan's sticky status, read by
+ * coll_m2d_device_status (synchronous) and cleared by
+ * coll_m2d_device_status_clear.
+ */
+typedef struct coll_m2d_plan_s* coll_m2d_plan;
+typedef struct {
+  int32_t N;
+  double L;
+  double S;
+  double b0;
+  int32_t A;
+  int32_t prec;
+  int32_t io_dtype;
+} coll_m2d_plan_desc;
+coll_status coll_m2d_plan_create(const coll_m2d_plan_desc* desc, coll_m2d_plan* out);
+coll_status coll_m2d_plan_destroy(coll_m2d_plan plan);
+coll_status coll_m2d_eval_batch(coll_m2d_plan plan, const void* f, void* Q, int64_t n_cells, coll_stream stream);
+coll_status coll_m2d_device_status(coll_m2d_plan plan);
+coll_status coll_m2d_device_status_clear(coll_m2d_plan plan);
+
+/*
  * f <- f + dt * Q for n elements (io_dtype 0: double, 1: float), the explicit
  * Euler step of the space-homogeneous equation df/dt = Q(f,f) (sec. 2, the
  * kinetic equation without transport).  Device pointers, f and Q distinct;

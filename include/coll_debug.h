@@ -24,6 +24,17 @@ coll_status coll_plan_tables_host(const coll_plan_desc* desc, double* out, size_
                                   size_t* n_doubles);
 
 /*
+ * coll_m2d_tables_host -- the table a 2D Maxwell plan would upload, built on
+ * the host without a GPU: (A + 1) * N * (N/2) pairs (A_t, B_t), layout
+ * [t][k0][k1 < N/2][2], k0 in FFT order, the loss pair last (see
+ * coll_m2d_plan_create).  out may be NULL to query the sizes; COLL_ENOMEM if
+ * cap (in doubles) is too small; COLL_EINVAL / COLL_EUNSUPPORTED like
+ * coll_m2d_plan_create.
+ */
+coll_status coll_m2d_tables_host(const coll_m2d_plan_desc* desc, double* out, size_t cap, int32_t* n_terms,
+                                 size_t* n_doubles);
+
+/*
  * coll_debug_mixed_drop_commit -- failure injection for the bounded waits of
  * the tensor-core path (COLL_MIXED_F16X2).  With on != 0, in every later
  * launch warpgroup 0 of each CTA omits the completion signal of its first MMA

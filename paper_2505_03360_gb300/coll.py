@@ -37,6 +37,11 @@ class coll_plan_desc(ctypes.Structure):
                 ("dealias", ctypes.c_int32), ("prec", ctypes.c_int32), ("io_dtype", ctypes.c_int32)]
 
 
+class coll_m2d_plan_desc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("L", ctypes.c_double), ("S", ctypes.c_double), ("b0", ctypes.c_double),
+                ("A", ctypes.c_int32), ("prec", ctypes.c_int32), ("io_dtype", ctypes.c_int32)]
+
+
 class coll_cell_group(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("f", ctypes.c_void_p), ("Q", ctypes.c_void_p)]
 
@@ -78,6 +83,13 @@ def _load():
         "coll_plan_tables_host": (I32, [ctypes.POINTER(coll_plan_desc), P, SZ, ctypes.POINTER(I32),
                                         ctypes.POINTER(SZ)]),
         "coll_debug_mixed_drop_commit": (I32, [I32]),
+        "coll_m2d_plan_create": (I32, [ctypes.POINTER(coll_m2d_plan_desc), ctypes.POINTER(P)]),
+        "coll_m2d_plan_destroy": (I32, [P]),
+        "coll_m2d_eval_batch": (I32, [P, P, P, I64, P]),
+        "coll_m2d_device_status": (I32, [P]),
+        "coll_m2d_device_status_clear": (I32, [P]),
+        "coll_m2d_tables_host": (I32, [ctypes.POINTER(coll_m2d_plan_desc), P, SZ, ctypes.POINTER(I32),
+                                       ctypes.POINTER(SZ)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -377,6 +389,85 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None):
             coll_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_m2d_desc(N, L, S=0.0, b0=-1.0, A=16, prec="f64", io_dtype=None) -> coll_m2d_plan_desc:
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    if io_dtype is None:
+        io_dtype = 1 if p == COLL_F32 else 0
+    return coll_m2d_plan_desc(int(N), float(L), float(S), float(b0), int(A), p, int(io_dtype))
+
+
+def coll_m2d_plan_create(desc: coll_m2d_plan_desc) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.coll_m2d_plan_create(ctypes.byref(desc), ctypes.byref(h)), "coll_m2d_plan_create")
+    return h.value
+
+
+def coll_m2d_plan_destroy(plan: int):
+    _check(_lib.coll_m2d_plan_destroy(ctypes.c_void_p(plan)), "coll_m2d_plan_destroy")
+
+
+def coll_m2d_eval_batch(plan: int, f, Q, n_cells: int, stream=None, check=True) -> int:
+    rc = _lib.coll_m2d_eval_batch(ctypes.c_void_p(plan), _ptr(f), _ptr(Q), int(n_cells), _stream_ptr(stream))
+    if check:
+        _check(rc, "coll_m2d_eval_batch")
+    return rc
+
+
+def coll_m2d_device_status(plan: int) -> int:
+    return int(_lib.coll_m2d_device_status(ctypes.c_void_p(plan)))
+
+
+def coll_m2d_device_status_clear(plan: int):
+    _check(_lib.coll_m2d_device_status_clear(ctypes.c_void_p(plan)), "coll_m2d_device_status_clear")
+
+
+def coll_m2d_tables_host(desc: coll_m2d_plan_desc):
+    """Host-built 2D table [A + 1, N, N/2, 2] (numpy, no GPU needed)."""
+    import numpy as np
+    nt, nd = ctypes.c_int32(), ctypes.c_size_t()
+    _check(_lib.coll_m2d_tables_host(ctypes.byref(desc), None, 0, ctypes.byref(nt), ctypes.byref(nd)),
+           "coll_m2d_tables_host")
+    out = np.empty(nd.value, dtype=np.float64)
+    _check(_lib.coll_m2d_tables_host(ctypes.byref(desc), out.ctypes.data_as(ctypes.c_void_p), nd.value,
+                                     ctypes.byref(nt), ctypes.byref(nd)), "coll_m2d_tables_host")
+    return out.reshape(nt.value, desc.N, desc.N // 2, 2)
+
+
+class Plan2D:
+    """RAII wrapper of a 2D Maxwell-molecule plan (coll_m2d_*)."""
+
+    def __init__(self, N, L, S=0.0, b0=-1.0, A=16, prec="f64", io_dtype=None, device=None):
+        import torch
+        self.desc = make_m2d_desc(N, L, S, b0, A, prec, io_dtype)
+        self.N = int(N)
+        self.torch_dtype = torch.float64 if self.desc.io_dtype == 0 else torch.float32
+        self.device = torch.device(device or "cuda")
+        with torch.cuda.device(self.device):
+            self.handle = coll_m2d_plan_create(self.desc)
+
+    def eval(self, f, Q=None, stream=None):
+        """Q for f [n, N, N] on the device (the plan's io dtype)."""
+        import torch
+        if Q is None:
+            Q = torch.empty_like(f)
+        coll_m2d_eval_batch(self.handle, f, Q, f.shape[0], stream=stream)
+        return Q
+
+    def status(self) -> int:
+        return coll_m2d_device_status(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            coll_m2d_plan_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -139,6 +139,24 @@ int launch_imex(int stage, const void* f, const void* Y, const void* Q1, const v
 int launch_esbgk(const void* f, const coll_moments* mom, bool io_f64, int N, double L, long long n_cells, double dt,
                  double eps, double beta, double mu0, void* out, void* stream);
 
+// 2D Maxwell-molecule operator (m2d_impl.cuh; m2d_d.cu, m2d_f.cu, m2d_x.cu)
+struct M2Args {
+  const void* f;
+  void* Q;
+  long long n_cells;
+  const void* tab;          // [n_terms][N][N/2] pairs (A, B) of the compute type
+  int n_terms;
+  int* status;
+};
+int m2d_launch_f64(int N, bool io_f64, const M2Args& a, int grid, void* stream);
+int m2d_occupancy_f64(int N, bool io_f64, int* ctas);
+int m2d_launch_f32(int N, bool io_f64, const M2Args& a, int grid, void* stream);
+int m2d_occupancy_f32(int N, bool io_f64, int* ctas);
+int m2d_launch_df(int N, bool io_f64, const M2Args& a, int grid, void* stream);
+int m2d_occupancy_df(int N, bool io_f64, int* ctas);
+// host tables: [n_terms][N][N/2][2] doubles, A gain terms then the loss term
+coll_status build_m2d_tables(const coll_m2d_plan_desc& d, int* n_terms, std::vector<double>* tab);
+
 // Host-side plan building (plan.cpp)
 struct HostTables {
   int n_terms;
@@ -164,5 +182,18 @@ struct coll_plan_s {
   coll::LayoutInfo lay[coll::kVariants];   // per slab-shape variant
   int ctas_per_sm[coll::kVariants];
   int variant;                             // chosen by coll_plan_autotune (default 0)
+  int num_sms;
+};
+
+struct coll_m2d_plan_s {
+  coll_m2d_plan_desc d;
+  int device;
+  int n_terms;
+  int ctype;         // coll::kCF64, kCF32 or kCDF
+  bool io_f64;
+  void* tab_dev;
+  size_t tab_bytes;
+  int* status_dev;
+  int ctas_per_sm;
   int num_sms;
 };

@@ -260,3 +260,29 @@ def regime_fields(ny: int, nx: int, dx: float, seed: int = BASE_SEED + 6):
     regimes = r.integers(0, 3, (ny, nx)).astype(np.uint8)
     l1 = 10.0 ** r.uniform(-5, -3, (ny, nx))
     return F, regimes, l1
+
+
+def bimodal_batch_2d(n_cells: int, N: int, L: float = 8.0, seed: int = BASE_SEED + 7,
+                     dtype=np.float64) -> np.ndarray:
+    """Two-dimensional cells: sum of two 2D Maxwellians per cell, densities
+    U[0.5, 2], mean velocities U[-1.5, 1.5]^2, temperatures U[0.5, 2]."""
+    r = rng(seed)
+    rho = r.uniform(0.5, 2.0, size=(n_cells, 2))
+    u = r.uniform(-1.5, 1.5, size=(n_cells, 2, 2))
+    T = r.uniform(0.5, 2.0, size=(n_cells, 2))
+    x = velocity_axis(N, L)
+    out = np.zeros((n_cells, N, N), dtype=np.float64)
+    for m in range(2):
+        g0 = np.exp(-(x[None, :] - u[:, m, 0:1]) ** 2 / (2.0 * T[:, m:m + 1]))
+        g1 = np.exp(-(x[None, :] - u[:, m, 1:2]) ** 2 / (2.0 * T[:, m:m + 1]))
+        amp = rho[:, m] / (2.0 * np.pi * T[:, m])
+        out += amp[:, None, None] * g0[:, :, None] * g1[:, None, :]
+    return out.astype(dtype)
+
+
+def bkw_datum_2d(N: int, L: float, S: float) -> np.ndarray:
+    """2D BKW datum for Maxwell molecules at shape parameter S >= 1/2:
+    exp(-|v|^2/(2S)) / (2 pi S^2) (2S - 1 + (1 - S)/(2S) |v|^2) (density 1)."""
+    x = velocity_axis(N, L)
+    v2 = x[:, None] ** 2 + x[None, :] ** 2
+    return np.exp(-v2 / (2.0 * S)) / (2.0 * np.pi * S * S) * (2.0 * S - 1.0 + (1.0 - S) / (2.0 * S) * v2)

@@ -72,3 +72,26 @@ def test_tables_reject_bad_desc():
     bad = coll.make_desc(16, 8.0, M=30, Mtheta=4)      # Mphi odd
     with pytest.raises(coll.CollError):
         coll.coll_plan_tables_host(bad)
+
+
+@pytest.mark.parametrize("N,L,A,S", [(16, 8.0, 8, 0.0), (32, 10.0, 16, 3.5), (64, 8.0, 5, 0.0)])
+def test_m2d_tables_match_oracle(N, L, A, S):
+    from oracle import maxwell2d as m2
+    tab = coll.coll_m2d_tables_host(coll.make_m2d_desc(N, L, S=S, A=A))
+    c, al, alp, lam = m2.multipliers(m2.Params2D(N=N, L=L, S=S, A=A))
+    H = N // 2
+    ref = np.zeros((A + 1, N, H, 2))
+    ref[:A, ..., 0] = c * al[:, :, :H] / N ** 2
+    ref[:A, ..., 1] = alp[:, :, :H] / N ** 2
+    ref[A, ..., 0] = -lam[:, :H] / N ** 2
+    ref[A, ..., 1] = 1.0 / N ** 2
+    ref[:, H] = 0.0                                   # Nyquist row dropped
+    assert tab.shape == ref.shape
+    assert np.max(np.abs(tab - ref)) <= 1e-14 * np.max(np.abs(ref))
+
+
+def test_m2d_reject_bad_desc():
+    for kw in (dict(N=15, L=8.0), dict(N=16, L=0.0), dict(N=16, L=8.0, A=0), dict(N=16, L=8.0, S=-1.0)):
+        with pytest.raises(coll.CollError) as e:
+            coll.coll_m2d_tables_host(coll.make_m2d_desc(**kw))
+        assert e.value.status == coll.COLL_EINVAL
