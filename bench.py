@@ -54,6 +54,7 @@ KERNEL_SOURCES = {
     "moments_f64": ["moments.cu"],
     "mixed_f16_n32": ["mixed.cu", "tcgen05.cuh"],
     "mixed_sliced_n32": ["sliced.cu", "tcgen05.cuh", "dfloat.cuh"],
+    "m2d_f64_n32": ["m2d_impl.cuh", "m2d_d.cu", "fft.cuh", "twiddles.h"],
 }
 
 
@@ -106,6 +107,55 @@ def time_regime(torch, coll, synth, dev, ny, nx, reps):
     b.record(st)
     torch.cuda.synchronize(dev)
     return a.elapsed_time(b) / reps
+
+
+M2D_WORKLOAD = dict(N=32, L=8.0, A=32, cells=32768)
+
+
+def m2d_flops_per_cell(N: int, A: int) -> float:
+    """2D operator, counted like the 3D one: 2 A + 3 real 2D transforms of N^2
+    points, each 2.5 N^2 log2(N^2) flops, plus 4 flops per gain term per point
+    and 3 per point for the loss."""
+    n2 = N * N
+    return (2 * A + 3) * 2.5 * n2 * math.log2(n2) + 4 * A * n2 + 3 * n2
+
+
+def fp32_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
+    """FP32 pipe peak: 128 FFMA per clock per SM (256 flop)."""
+    return sms * 256 * sm_mhz * 1e6 / 1e12
+
+
+def time_m2d(torch, coll, synth, dev, reps=5):
+    """2D Maxwell molecules (coll_m2d_eval_batch): FP64, float pairs and FP32 on
+    32768 cells N = 32^2 (f and Q 268 MB each in FP64, larger than L2)."""
+    w = M2D_WORKLOAD
+    N, A, n = w["N"], w["A"], w["cells"]
+    f64 = torch.from_numpy(synth.bimodal_batch_2d(n, N, w["L"])).to(dev)
+    st = torch.cuda.Stream(device=dev)
+    out, ref = {}, None
+    for prec in ("f64", "f32x2", "f32"):
+        plan = coll.Plan2D(N, w["L"], A=A, prec=prec, device=dev)
+        fd = f64.to(plan.torch_dtype)
+        Q = torch.empty_like(fd)
+        for _ in range(3):
+            plan.eval(fd, Q, stream=st)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            plan.eval(fd, Q, stream=st)
+        b.record(st)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / reps
+        if prec == "f64":
+            ref = Q
+            err = 0.0
+        else:
+            err = float(torch.linalg.vector_norm(Q.double() - ref) / torch.linalg.vector_norm(ref))
+        out[prec] = (ms, err, plan.status())
+        plan.close()
+    del f64
+    return out
 
 
 def max_over_ranks(x: float, world: int, device=None) -> float:
@@ -268,6 +318,18 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    if args.profile_m2d:
+        # short capture target: the 2D operator alone on --m2d-cells cells, two launches
+        mw = M2D_WORKLOAD
+        plan2 = coll.Plan2D(mw["N"], mw["L"], A=mw["A"], prec=args.profile_m2d, device=dev)
+        f2 = torch.from_numpy(synth.bimodal_batch_2d(args.m2d_cells, mw["N"], mw["L"])).to(dev).to(plan2.torch_dtype)
+        Q2 = torch.empty_like(f2)
+        for _ in range(2):
+            plan2.eval(f2, Q2)
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"profile_m2d": args.profile_m2d, "cells": args.m2d_cells, "status": plan2.status()}))
+        plan2.close()
+        return
     w = WORKLOAD
     N, n = w["N"], args.cells
     f_host = synth.bimodal_batch(n, N, w["L"], seed=synth.BASE_SEED + 2 + 1000 * rank)
@@ -626,6 +688,31 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "achieved": es_tf, "peak": peak, "unit": "TFLOP/s", "frac": es_tf / peak,
                      "peak_basis": "FP64 pipe (as the main line)", "flops_per_value": ESBGK_FP64_OPS_PER_VALUE,
                      "hbm_gbs": es_bytes / (t_es / 1e3) / 1e9, "bytes_per_launch": es_bytes}}
+    # 2D Maxwell molecules (sec. 4.4.1, "The 2d case"): 32768 cells N = 32^2, A = 32 angles
+    mw = M2D_WORKLOAD
+    m2 = time_m2d(torch, coll, synth, dev)
+    m2_flops = m2d_flops_per_cell(mw["N"], mw["A"]) * mw["cells"]
+    t64 = m2["f64"][0]
+    t32m = m2["f32"][0]
+    p32 = fp32_peak_tflops(sm_for_peak)
+    line["maxwell2d"] = {
+        "kernel": "m2d_kernel<32, T, Tio> (2D Maxwell molecules, one CTA per cell, 8 terms side by side)",
+        "workload": "%d cells, N = %d^2, A = %d angles (%d terms with the loss), L = %g, R = 2S, "
+                    "S = 2L/(3 + sqrt 2); bimodal 2D Maxwellians" % (mw["cells"], mw["N"], mw["A"], mw["A"] + 1,
+                                                                    mw["L"]),
+        "f64": {"ms_per_launch": t64, "cell_evals_per_s": mw["cells"] / (t64 / 1e3), "status": m2["f64"][2],
+                "roofline": {"bound": "alu", "achieved": m2_flops / (t64 / 1e3) / 1e12, "peak": peak,
+                             "unit": "TFLOP/s", "frac": m2_flops / (t64 / 1e3) / 1e12 / peak,
+                             "peak_basis": "FP64 pipe (as the main line)", "flops_per_launch": m2_flops,
+                             "traffic": load_traffic("m2d_f64_n32")}},
+        "f32x2": {"ms_per_launch": m2["f32x2"][0], "cell_evals_per_s": mw["cells"] / (m2["f32x2"][0] / 1e3),
+                  "rel_l2_vs_f64": m2["f32x2"][1], "status": m2["f32x2"][2]},
+        "f32": {"ms_per_launch": t32m, "cell_evals_per_s": mw["cells"] / (t32m / 1e3), "rel_l2_vs_f64": m2["f32"][1],
+                "status": m2["f32"][2],
+                "roofline": {"bound": "alu", "achieved": m2_flops / (t32m / 1e3) / 1e12, "peak": p32,
+                             "unit": "TFLOP/s", "frac": m2_flops / (t32m / 1e3) / 1e12 / p32,
+                             "peak_basis": "FP32 pipe, 152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz (derived)",
+                             "hbm_gbs": 2 * mw["cells"] * mw["N"] ** 2 * 4 / (t32m / 1e3) / 1e9}}}
     if args.serve_requests > 0:
         from paper_2505_03360_gb300.service import Service, stream_jobs
         svc = Service(hbm_budget_bytes=120e9, device=str(dev))
@@ -666,6 +753,9 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=100,
                     help="requests of the serving stream measured beside the main line (0: skip)")
     ap.add_argument("--serve-max-cells", type=int, default=64)
+    ap.add_argument("--profile-m2d", default=None, choices=["f64", "f32x2", "f32"],
+                    help="run only the 2D Maxwell operator (two launches) for profiler captures")
+    ap.add_argument("--m2d-cells", type=int, default=M2D_WORKLOAD["cells"])
     ap.add_argument("--prec", default="f64", choices=["f64", "f32x2", "f32", "mixed_f16x2", "mixed_bf16x3",
                                                       "mixed_sliced"],
                     help="compute precision of the main path in --profile-only runs")

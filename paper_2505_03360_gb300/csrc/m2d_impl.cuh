@@ -12,12 +12,13 @@
 // (-Lambda / N^2, 1 / N^2) for the loss term (the plan's table).  The grid
 // offset v_0 = -L cancels because every multiplier is real and even.
 //
-// A 2D cell has only N pencils per axis, too few for a CTA, so TB = 256 / N
-// terms run side by side: pass A (thread = term, column k1) forms the
+// A 2D cell has only N pencils per axis, too few for a CTA, so TB terms run
+// side by side (TB N threads; 128 threads for N <= 32, so that two CTAs share
+// an SM and one's barriers and partial batches overlap the other's work): pass A (thread = term, column k1) forms the
 // column of (A + iB) F from the half spectrum and transforms it along k0;
 // pass B (thread = term, row v0) transforms the row along k1 and writes
 // Re * Im over the row it has just read; a reduction over the TB terms adds
-// the products into the gain accumulator, which lives in registers (N^2 / 256
+// the products into the gain accumulator, which lives in registers (N^2 / (TB N)
 // values per thread).  Every array is in shared memory: nothing but f, Q and
 // the table touches global memory.
 #pragma once
@@ -29,19 +30,18 @@
 
 namespace coll {
 
-constexpr int kM2Threads = 256;
-
 template <int N, typename T> struct M2Lay {
   using V2 = typename C2<T>::type;
   static constexpr int H = N / 2;
-  static constexpr int TB = kM2Threads / N;            // terms side by side
+  static constexpr int TB = N == 64 ? 4 : 128 / N;    // terms side by side
+  static constexpr int THREADS = TB * N;
   static constexpr int WR = N + 1;                     // W row pitch (complex), conflict-free rows
   static constexpr int FR = H + 1;                     // Fh row pitch (complex)
-  static constexpr int E = N * N / kM2Threads;         // accumulator values per thread
+  static constexpr int E = N * N / THREADS;            // accumulator values per thread
   static constexpr size_t W_BYTES = size_t(TB) * N * WR * sizeof(V2);
   static constexpr size_t FH_BYTES = size_t(N) * FR * sizeof(V2);
   static constexpr size_t SMEM = W_BYTES + FH_BYTES;
-  static_assert(N * N % kM2Threads == 0 && kM2Threads % N == 0, "N in {16, 32, 64}");
+  static_assert(N == 16 || N == 32 || N == 64, "N in {16, 32, 64}");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -55,10 +55,10 @@ __device__ __forceinline__ bool m2_finite(double x) { return ::isfinite(x); }
 __device__ __forceinline__ bool m2_finite(float x) { return ::isfinite(x); }
 
 template <int N, typename T, typename Tio>
-__global__ void __launch_bounds__(kM2Threads, 1) m2d_kernel(M2Args a) {
+__global__ void __launch_bounds__(M2Lay<N, T>::THREADS, 1) m2d_kernel(M2Args a) {
   using Ly = M2Lay<N, T>;
   using V2 = typename Ly::V2;
-  constexpr int H = Ly::H, TB = Ly::TB, WR = Ly::WR, FR = Ly::FR, E = Ly::E;
+  constexpr int H = Ly::H, TB = Ly::TB, WR = Ly::WR, FR = Ly::FR, E = Ly::E, NT = Ly::THREADS;
   extern __shared__ __align__(16) unsigned char smem[];
   V2* W = reinterpret_cast<V2*>(smem);
   V2* Fh = reinterpret_cast<V2*>(smem + Ly::W_BYTES);
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kM2Threads, 1) m2d_kernel(M2Args a) {
   for (long long c = blockIdx.x; c < a.n_cells; c += gridDim.x) {
     const Tio* f = static_cast<const Tio*>(a.f) + size_t(c) * N * N;
     __syncthreads();                                     // the previous cell is done with W
-    for (int i = tid; i < N * N; i += kM2Threads) fs[(i / N) * (N + 1) + i % N] = f[i];
+    for (int i = tid; i < N * N; i += NT) fs[(i / N) * (N + 1) + i % N] = f[i];
     __syncthreads();
 
     // forward, axis 1: rows p and p + N/2 packed into one complex transform,
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kM2Threads, 1) m2d_kernel(M2Args a) {
       const int nb = a.n_terms - t0 < TB ? a.n_terms - t0 : TB;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        const int idx = tid + e * kM2Threads, v0 = idx / N, v1 = idx % N;
+        const int idx = tid + e * NT, v0 = idx / N, v1 = idx % N;
         T s = G[e];
         for (int b = 0; b < nb; ++b) s = s + reinterpret_cast<const T*>(W + (size_t(b) * N + v0) * WR)[v1];
         G[e] = s;
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kM2Threads, 1) m2d_kernel(M2Args a) {
     for (int e = 0; e < E; ++e) {
       const Tio q = m2_st<Tio, T>(G[e]);
       bad |= !m2_finite(q);
-      Q[tid + e * kM2Threads] = q;
+      Q[tid + e * NT] = q;
     }
   }
   if (__syncthreads_or(bad) && tid == 0) atomicOr(a.status, kStatusNonFinite);
@@ -186,7 +186,7 @@ int m2d_launch_t(const M2Args& a, int grid, cudaStream_t st) {
   constexpr size_t smem = M2Lay<N, T>::SMEM;
   const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return int(e);
-  k<<<grid, kM2Threads, smem, st>>>(a);
+  k<<<grid, M2Lay<N, T>::THREADS, smem, st>>>(a);
   return int(cudaGetLastError());
 }
 
@@ -196,7 +196,7 @@ int m2d_occupancy_t(int* ctas) {
   constexpr size_t smem = M2Lay<N, T>::SMEM;
   const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return int(e);
-  return int(cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k, kM2Threads, smem));
+  return int(cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k, M2Lay<N, T>::THREADS, smem));
 }
 
 

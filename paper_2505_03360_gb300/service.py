@@ -89,6 +89,7 @@ class Service:
         # tensor-core launches (one per mixed request, few CTAs each) run concurrently on side streams
         self.side = [torch.cuda.Stream(device=self.device) for _ in range(8)]
         self.ws = None
+        self.lane_ws = {}
         self.in_use = 0
         self.peak_in_use = 0
         self.stats = collections.Counter()
@@ -107,19 +108,41 @@ class Service:
         return self.plans[key]
 
     def _mix_plan(self, j, lane):
-        """Tensor-core plan for job j on side stream `lane` (each lane owns its workspace)."""
-        key = (j.N, float(j.lam), "mixed_f16x2", lane)
-        if key not in self.plans:
-            Mr = 16 if j.lam == 1.0 else 8
-            self.plans[key] = coll.Plan(j.N, self.L, lam=j.lam, M=self.M, Mtheta=self.Mtheta, Mr=Mr,
-                                        prec="mixed_f16x2", io_dtype=1, max_cells=1, device=self.device)
-        return self.plans[key]
+        """Tensor-core plan for job j and the workspace of side stream `lane`: one
+        plan per (N, lambda) serves every lane (a plan is immutable; each
+        concurrent launch needs only its own workspace)."""
+        p = self.plan(j.N, j.lam, "mixed_f16x2")
+        need = max(256, coll.coll_workspace_size(p.handle, max(1, j.n_cells)))
+        ws = self.lane_ws.get(lane)
+        if ws is None or ws.numel() < need:
+            self.side[lane].synchronize()            # the old buffer may still be in use on the lane
+            ws = self.torch.empty(need, dtype=self.torch.uint8, device=self.device)
+            self.lane_ws[lane] = ws
+        return p, ws
 
     def warm_plans(self, Ns=(16, 32, 48, 64), lams=(0.0, 1.0), precisions=("f32", "mixed")):
+        """Build every plan the stream can ask for and launch each kernel once on one
+        zero cell, so that table building and module loading stay out of serving."""
+        torch = self.torch
         for N in Ns:
             for lam in lams:
                 for p in precisions:
-                    self.plan(N, lam, effective_precision(p, N))
+                    prec = effective_precision(p, N)
+                    plan = self.plan(N, lam, prec)
+                    dt = torch.float64 if prec in ("f32x2", "f64") else torch.float32
+                    f = torch.zeros((1, N, N, N), dtype=dt, device=self.device)
+                    Q = torch.empty_like(f)
+                    if prec == "mixed_f16x2":
+                        for lane in range(len(self.side)):
+                            j = Job(rid=-1, arrival_s=0.0, n_cells=1, N=N, lam=lam, precision=p)
+                            pl, ws = self._mix_plan(j, lane)
+                            coll.coll_eval_batch(pl.handle, f, Q, 1, ws, stream=self.side[lane])
+                    else:
+                        groups = [(plan.handle, f, Q)]
+                        self._ensure_ws(coll.coll_ragged_workspace_size(groups, [1]))
+                        coll.coll_eval_ragged(groups, [1], self.ws, stream=self.stream)
+                        coll.coll_advance(f, Q, 0.0, stream=self.stream)
+        torch.cuda.synchronize(self.device)
 
     # -------------------------------------------------------------- memory
     def _job_bytes(self, j: Job) -> int:
@@ -176,8 +199,8 @@ class Service:
                 for i, j in enumerate(jobs):
                     st = self.side[i % len(self.side)]
                     st.wait_event(ready)
-                    p = self._mix_plan(j, i % len(self.side))
-                    coll.coll_eval_batch(p.handle, j.f, j.Q, j.n_cells, p.reserve(j.n_cells), stream=st)
+                    p, ws = self._mix_plan(j, i % len(self.side))
+                    coll.coll_eval_batch(p.handle, j.f, j.Q, j.n_cells, ws, stream=st)
                     self.stats["launches"] += 1
                     if st not in side_used:
                         side_used.append(st)
@@ -268,9 +291,11 @@ class Service:
         return finished, stats
 
     def close(self):
+        self.torch.cuda.synchronize(self.device)
         for p in self.plans.values():
             p.close()
         self.plans.clear()
+        self.lane_ws.clear()
 
 
 def stream_jobs(n_requests=2000, rate_per_s=200.0, seed=synth.BASE_SEED + 5, max_cells=2048,
