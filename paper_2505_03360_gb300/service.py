@@ -121,8 +121,10 @@ class Service:
         return p, ws
 
     def warm_plans(self, Ns=(16, 32, 48, 64), lams=(0.0, 1.0), precisions=("f32", "mixed")):
-        """Build every plan the stream can ask for and launch each kernel once on one
-        zero cell, so that table building and module loading stay out of serving."""
+        """Build every plan the stream can ask for, launch each kernel once on one
+        zero cell and run the synthetic request generator once per (N, dtype), so
+        that table building, module loading and first-use compilation stay out of
+        serving."""
         torch = self.torch
         for N in Ns:
             for lam in lams:
@@ -142,6 +144,9 @@ class Service:
                         self._ensure_ws(coll.coll_ragged_workspace_size(groups, [1]))
                         coll.coll_eval_ragged(groups, [1], self.ws, stream=self.stream)
                         coll.coll_advance(f, Q, 0.0, stream=self.stream)
+                    # the device-side request generator's own kernels (first use may JIT-compile them)
+                    with torch.cuda.stream(self.stream):
+                        synth.bimodal_batch_device(1, N, self.L, 0, dtype=dt, device=self.device)
         torch.cuda.synchronize(self.device)
 
     # -------------------------------------------------------------- memory
