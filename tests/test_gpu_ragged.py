@@ -107,3 +107,41 @@ def test_ragged_errors():
     assert coll.coll_eval_ragged(ok, [0], ws, check=False) == coll.COLL_OK
     p32.close()
     p64.close()
+
+
+def test_config4_full_workload_graph():
+    """The full uneven batch of the 256 x 256 regime mask (about 10 K FP32 cells, N in
+    {16, 24, 32, 48}, hard spheres, M = 48, Mr = 16) in one ragged launch replayed from
+    a CUDA graph, the configuration bench.py times: every group equals its own
+    coll_eval_batch bitwise, and the first and last cell of each group match the
+    oracle within the FP32 tolerance."""
+    rb = synth.ragged_batch(L=L)
+    plans, groups, cells = [], [], []
+    for N in synth.RAGGED_N:
+        g = rb.groups[N]
+        p = coll.Plan(N, L, lam=1.0, M=48, Mtheta=4, Mr=16, prec="f32", max_cells=max(1, g.shape[0]))
+        f = torch.from_numpy(g).cuda()
+        plans.append(p)
+        groups.append((p.handle, f, torch.full_like(f, float("nan"))))
+        cells.append(g.shape[0])
+    assert sum(cells) == int(rb.mask.sum()) and 0.145 <= rb.mask.mean() <= 0.155
+    ws = torch.empty(coll.coll_ragged_workspace_size(groups, cells), dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=s):
+            coll.coll_eval_ragged(groups, cells, ws, stream=s)
+        graph.replay()
+    torch.cuda.synchronize()
+    for p, (h, f, Q), N, n in zip(plans, groups, synth.RAGGED_N, cells):
+        assert p.status() == coll.COLL_OK
+        assert torch.equal(Q, p.eval(f)), N
+        pr = Params(N=N, L=L, lam=1.0, M=48, Mtheta=4, Mr=16)
+        m = multipliers(pr)
+        for c in (0, n - 1):
+            want = q_fast(f[c].double().cpu().numpy(), pr, m)
+            got = Q[c].double().cpu().numpy()
+            assert np.linalg.norm(got - want) / np.linalg.norm(want) <= TOL["f32"], (N, c)
+    for p in plans:
+        p.close()

@@ -116,3 +116,26 @@ def test_sliced_unsupported_shapes():
         with pytest.raises(coll.CollError) as e:
             coll.Plan(N, L, lam=1.0, M=32, Mtheta=4, Mr=8, prec="mixed_sliced")
         assert e.value.status == coll.COLL_EUNSUPPORTED
+
+
+def test_sliced_full_batch_config3():
+    """The bench's 4096-cell N = 32 hard-sphere batch (same seed and launch
+    configuration): every cell within 1e-6 of the FP64 path, and sampled cells
+    within 1e-6 of the oracle."""
+    N, n = 32, 4096
+    fnp = synth.bimodal_batch(n, N, L, seed=synth.BASE_SEED + 2)
+    f = torch.from_numpy(fnp).cuda()
+    ps = coll.Plan(N, L, lam=1.0, M=48, Mtheta=4, Mr=16, prec="mixed_sliced", max_cells=n)
+    p64 = coll.Plan(N, L, lam=1.0, M=48, Mtheta=4, Mr=16, prec="f64", max_cells=n)
+    qs, q64 = ps.eval(f), p64.eval(f)
+    torch.cuda.synchronize()
+    assert ps.status() == coll.COLL_OK and p64.status() == coll.COLL_OK
+    err = torch.linalg.norm((qs - q64).reshape(n, -1), dim=1) / torch.linalg.norm(q64.reshape(n, -1), dim=1)
+    assert float(err.max()) <= TOL, float(err.max())
+    pr = Params(N=N, L=L, lam=1.0, M=48, Mtheta=4, Mr=16)
+    m = multipliers(pr)
+    worst = int(torch.argmax(err))
+    for c in sorted({0, 2047, n - 1, worst}):
+        assert rel(qs[c].cpu().numpy(), q_fast(fnp[c], pr, m)) <= TOL, c
+    ps.close()
+    p64.close()
