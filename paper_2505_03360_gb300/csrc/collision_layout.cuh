@@ -45,8 +45,8 @@ COLL_CFG(32, df,     0,  4, true, false, true,  true)
 COLL_CFG(16, float,  0,  1, true, true,  true,  true)
 COLL_CFG(24, float,  0,  1, true, true,  true,  false)
 COLL_CFG_P1F(32, float,  0, 4, true, false)
-COLL_CFG(48, float,  0,  8, true, false, true,  true)
-COLL_CFG(64, float,  0,  8, false, false, true, true)
+COLL_CFG_P1F(48, float, 0, 8, false, true)
+COLL_CFG_P1F(64, float, 0, 16, false, true)
 COLL_CFG(16, double, 1,  2, true, true,  true,  true)
 COLL_CFG(24, double, 1,  4, true, true,  true,  true)
 COLL_CFG(32, double, 1,  8, true, false, true,  true)
@@ -56,8 +56,8 @@ COLL_CFG(32, df,     1,  8, true, false, true,  true)
 COLL_CFG(16, float,  1,  2, true, true,  true,  true)
 COLL_CFG(24, float,  1,  2, true, true,  true,  true)
 COLL_CFG(32, float,  1,  2, true, false, true,  true)
-COLL_CFG(48, float,  1,  4, true, false, false, true)
-COLL_CFG(64, float,  1, 16, true, false, true,  true)
+COLL_CFG(48, float,  1,  8, true, false, true,  true)
+COLL_CFG(64, float,  1,  8, false, false, true, true)
 #undef COLL_CFG
 #undef COLL_CFG_P1F
 
