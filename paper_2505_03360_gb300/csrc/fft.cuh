@@ -165,6 +165,7 @@ template <> struct TwFma<float> {
 };
 template <typename T> constexpr bool kFmaFft = false;
 template <> constexpr bool kFmaFft<double> = true;
+template <> constexpr bool kFmaFft<float> = true;
 
 __host__ __device__ constexpr bool tw_trivial(int n) { return n % 48 == 0; }
 __host__ __device__ constexpr int tw_form(int n) { return (n % 96 <= 24 || n % 96 >= 72) ? 0 : 1; }
