@@ -139,7 +139,7 @@ __device__ __forceinline__ void unscramble(const T* sr, const T* si, T* dr, T* d
 }
 
 // ------------------------------------------------- decimation in time, FMA form
-// For FP64 and power-of-two lengths the transform is a decimation-in-time
+// For FP64 and FP32 the transform is a decimation-in-time
 // recursion instead: its butterflies take twiddled INPUTS, so each generic
 // twiddle folds into fused multiply-adds.  With w = exp(SIGN 2 pi i n / 192),
 //   form 0 (|cos| >= |sin|): w y = m u, m = cos, u = y + i tan * y
@@ -278,6 +278,35 @@ __device__ __forceinline__ void dit_comb4(T* yr, T* yi, int b, int M, int j) {
   yr[b + 3 * M] = fma(ss, Di, Br); yi[b + 3 * M] = fma(-ss, Dr, Bi);
 }
 
+// radix-3 combine at (b + q M), q < 3: X_p = sum_q w3^{pq} w_L^{qj} y_q.  Within the
+// supported lengths (radix 4 first, so 3 is always the innermost factor) j = 0 and the
+// twiddles are trivial; a generic twiddle is applied as a plain product.
+template <int L, int SIGN, typename T>
+__device__ __forceinline__ void dit_comb3(T* yr, T* yi, int b, int M, int j) {
+  T a0r = yr[b], a0i = yi[b], a1r = yr[b + M], a1i = yi[b + M], a2r = yr[b + 2 * M], a2i = yi[b + 2 * M];
+#pragma unroll
+  for (int q = 1; q < 3; ++q) {
+    const int n = ((q * j) % L) * (192 / L);
+    T& r = q == 1 ? a1r : a2r;
+    T& i = q == 1 ? a1i : a2i;
+    if (tw_trivial(n)) {
+      tw_exact<SIGN>(r, i, n);
+    } else {
+      T ur, ui;
+      const T m = tw_fma<SIGN>(r, i, n, ur, ui);
+      r = m * ur;
+      i = m * ui;
+    }
+  }
+  const T h = Tw<T>::s(64);                 // sin(2 pi / 3) = sqrt(3)/2
+  const T tr = a1r + a2r, ti = a1i + a2i, dr = a1r - a2r, di = a1i - a2i;
+  const T mr = fma(T(-0.5), tr, a0r), mi = fma(T(-0.5), ti, a0i);
+  const T vr = SIGN > 0 ? -h * di : h * di, vi = SIGN > 0 ? h * dr : -h * dr;   // SIGN i h d
+  yr[b] = a0r + tr; yi[b] = a0i + ti;
+  yr[b + M] = mr + vr; yi[b + M] = mi + vi;
+  yr[b + 2 * M] = mr - vr; yi[b + 2 * M] = mi - vi;
+}
+
 template <int L, int OFF, int STRIDE, int OB, int SIGN, typename T>
 __device__ __forceinline__ void dit(const T* xr, const T* xi, T* yr, T* yi);
 
@@ -298,11 +327,12 @@ __device__ __forceinline__ void dit(const T* xr, const T* xi, T* yr, T* yi) {
     yi[OB] = xi[OFF];
   } else {
     constexpr int R = radix_of(L), M = L / R;
-    static_assert(R == 2 || R == 4, "power-of-two lengths only");
+    static_assert(R == 2 || R == 3 || R == 4, "lengths 2^a 3^b");
     dit_subs<L, OFF, STRIDE, OB, SIGN, T, 0>(xr, xi, yr, yi);
 #pragma unroll
     for (int j = 0; j < M; ++j) {
       if constexpr (R == 4) dit_comb4<L, SIGN, T>(yr, yi, OB + j, M, j);
+      else if constexpr (R == 3) dit_comb3<L, SIGN, T>(yr, yi, OB + j, M, j);
       else dit_comb2<L, SIGN, T>(yr, yi, OB + j, M, j);
     }
   }
@@ -311,7 +341,7 @@ __device__ __forceinline__ void dit(const T* xr, const T* xi, T* yr, T* yi) {
 // In-place length-L transform of (re, im), natural order in and out.
 template <int L, int SIGN, typename T>
 __device__ __forceinline__ void fft(T* re, T* im) {
-  if constexpr (kFmaFft<T> && is_pow2(L)) {
+  if constexpr (kFmaFft<T>) {
     T tr[L], ti[L];
     dit<L, 0, 1, 0, SIGN, T>(re, im, tr, ti);
 #pragma unroll
