@@ -86,6 +86,7 @@ coll_status ragged_prepare(const coll_cell_group* groups, const int64_t* cells, 
     it.status = g.plan->status_dev;
     it.N = g.plan->d.N;
     it.n_terms = g.plan->n_terms;
+    it.variant = g.plan->variant;
     acc += it.n_cells;
   }
   t->total_units = acc;

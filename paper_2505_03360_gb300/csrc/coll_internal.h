@@ -100,6 +100,7 @@ struct RaggedItem {            // one group of cells evaluated with one plan
   int* status;
   int N;
   int n_terms;
+  int variant;                 // the plan's slab shape (coll_plan_autotune / coll_plan_set_variant)
 };
 struct RaggedTable {
   RaggedItem items[kMaxRaggedGroups];

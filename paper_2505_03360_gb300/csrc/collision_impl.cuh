@@ -323,20 +323,19 @@ __device__ __forceinline__ void process_cell(const Tio* __restrict__ f, Tio* __r
         }
       }
     }
-    return;
-  }
-
-  for (int s = 0; s < S0; ++s) {
-    for (int i = threadIdx.x; i < NS * N * (N + 1); i += kThreads) G[i] = T{};
-    __syncthreads();
-    for (int t = 0; t < n_terms; ++t) {
-      run_p1<N, T, V>(tab + size_t(t) * N * N * H, Fh, W, s);
+  } else {
+    for (int s = 0; s < S0; ++s) {
+      for (int i = threadIdx.x; i < NS * N * (N + 1); i += kThreads) G[i] = T{};
       __syncthreads();
-      run_pass<N, T, Tio>(kPassInv, W, NS * N, N, N * WR, 1, WR, H, f, Q, G, s, S0, FR, false);
-      __syncthreads();
-      bad |= run_pass<N, T, Tio>(kPassP3, W, NS * N, N, N * WR, WR, 1, -1, f, Q, G, s, S0, FR,
-                                 t == n_terms - 1);
-      __syncthreads();
+      for (int t = 0; t < n_terms; ++t) {
+        run_p1<N, T, V>(tab + size_t(t) * N * N * H, Fh, W, s);
+        __syncthreads();
+        run_pass<N, T, Tio>(kPassInv, W, NS * N, N, N * WR, 1, WR, H, f, Q, G, s, S0, FR, false);
+        __syncthreads();
+        bad |= run_pass<N, T, Tio>(kPassP3, W, NS * N, N, N * WR, WR, 1, -1, f, Q, G, s, S0, FR,
+                                   t == n_terms - 1);
+        __syncthreads();
+      }
     }
   }
 }
@@ -363,16 +362,32 @@ struct RaggedDispatch;
 
 template <typename T, typename Tio>
 struct RaggedDispatch<T, Tio> {
-  static __device__ __forceinline__ void run(int, const Tio*, Tio*, const typename C2<T>::type*, int, unsigned char*,
-                                             unsigned char*, bool&) {}
+  static __device__ __forceinline__ void run(int, int, const Tio*, Tio*, const typename C2<T>::type*, int,
+                                             unsigned char*, unsigned char*, bool&) {}
 };
 
+// One cell in one (N, slab shape) as a separate function: each body gets its own
+// register allocation instead of the union of all of them inside the ragged kernel.
+template <int N, typename T, typename Tio, int V>
+__device__ __noinline__ bool ragged_cell(const Tio* f, Tio* Q, const typename C2<T>::type* tab, int nt,
+                                         unsigned char* smem, unsigned char* wsc) {
+  bool bad = false;
+  process_cell<N, T, Tio, V>(f, Q, tab, nt, smem, wsc, bad);
+  return bad;
+}
+
+// per-N body in the slab shape the group's plan uses (so that a ragged launch
+// equals coll_eval_batch of each group alone, whichever shape the autotuner chose)
 template <typename T, typename Tio, int N0, int... Ns>
 struct RaggedDispatch<T, Tio, N0, Ns...> {
-  static __device__ __forceinline__ void run(int N, const Tio* f, Tio* Q, const typename C2<T>::type* tab, int nt,
-                                             unsigned char* smem, unsigned char* wsc, bool& bad) {
-    if (N == N0) process_cell<N0, T, Tio>(f, Q, tab, nt, smem, wsc, bad);
-    else RaggedDispatch<T, Tio, Ns...>::run(N, f, Q, tab, nt, smem, wsc, bad);
+  static __device__ __forceinline__ void run(int N, int V, const Tio* f, Tio* Q, const typename C2<T>::type* tab,
+                                             int nt, unsigned char* smem, unsigned char* wsc, bool& bad) {
+    if (N == N0) {
+      if (V == 1) bad |= ragged_cell<N0, T, Tio, 1>(f, Q, tab, nt, smem, wsc);
+      else bad |= ragged_cell<N0, T, Tio, 0>(f, Q, tab, nt, smem, wsc);
+    } else {
+      RaggedDispatch<T, Tio, Ns...>::run(N, V, f, Q, tab, nt, smem, wsc, bad);
+    }
   }
 };
 
@@ -397,7 +412,8 @@ __global__ void __launch_bounds__(kThreads, 1) ragged_kernel(RaggedTable tbl, vo
     const long long c = u - it.first_unit;
     const size_t n3 = size_t(it.N) * it.N * it.N;
     bool bad = false;
-    RaggedDispatch<T, Tio, Ns...>::run(it.N, static_cast<const Tio*>(it.f) + c * n3, static_cast<Tio*>(it.Q) + c * n3,
+    RaggedDispatch<T, Tio, Ns...>::run(it.N, it.variant, static_cast<const Tio*>(it.f) + c * n3,
+                                       static_cast<Tio*>(it.Q) + c * n3,
                                        static_cast<const typename C2<T>::type*>(it.tab), it.n_terms, smem, wsc, bad);
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(it.status, kStatusNonFinite);
   }
@@ -405,14 +421,14 @@ __global__ void __launch_bounds__(kThreads, 1) ragged_kernel(RaggedTable tbl, vo
 
 template <typename T, typename Tio, int... Ns>
 struct RaggedLaunch {
-  static constexpr size_t smem() {
+  static constexpr size_t smem() {      // the largest of every N's two slab shapes
     size_t m = 0;
-    for (size_t v : {Lay<Ns, T>::SMEM...}) m = v > m ? v : m;
+    for (size_t v : {Lay<Ns, T, 0>::SMEM..., Lay<Ns, T, 1>::SMEM...}) m = v > m ? v : m;
     return m;
   }
   static constexpr size_t ws() {        // per CTA: 256-byte header + the largest scratch
     size_t m = 0;
-    for (size_t v : {Lay<Ns, T>::WS...}) m = v > m ? v : m;
+    for (size_t v : {Lay<Ns, T, 0>::WS..., Lay<Ns, T, 1>::WS...}) m = v > m ? v : m;
     return 256 + (m + 255) / 256 * 256;
   }
   static int launch(const RaggedTable& t, void* wsp, size_t ws_per_cta, int grid, cudaStream_t st) {

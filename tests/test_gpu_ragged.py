@@ -61,6 +61,24 @@ def test_ragged_equals_per_group_and_oracle(prec, Ns, counts):
         p.close()
 
 
+def test_ragged_honours_each_plans_slab_shape():
+    """Plans set to the second slab shape (as the autotuner may choose) are evaluated in
+    that shape inside the ragged launch: bitwise equal to their own coll_eval_batch."""
+    Ns, counts = [16, 32, 24, 48], [3, 2, 3, 1]
+    plans, fs, Qs = _groups("f32", Ns, counts, seed=21)
+    for p in plans[::2]:
+        coll.coll_plan_set_variant(p.handle, 1)
+    groups = [(p.handle, f, Q) for p, f, Q in zip(plans, fs, Qs)]
+    ws = torch.empty(coll.coll_ragged_workspace_size(groups, counts), dtype=torch.uint8, device="cuda")
+    coll.coll_eval_ragged(groups, counts, ws)
+    torch.cuda.synchronize()
+    for p, f, Q, N in zip(plans, fs, Qs, Ns):
+        assert p.status() == coll.COLL_OK
+        assert torch.equal(Q, p.eval(f)), N
+    for p in plans:
+        p.close()
+
+
 def test_ragged_cuda_graph_replay():
     """Memset + persistent launch captured in a CUDA graph; two replays equal eager."""
     Ns, counts = [16, 32, 24], [6, 3, 4]
