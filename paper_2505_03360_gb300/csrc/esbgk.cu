@@ -8,7 +8,7 @@
 //   out = eps/(eps + nu dt) f + nu dt/(eps + nu dt) G[f^{n+1}],
 //   G = rho / sqrt(det(2 pi Tau)) exp(-(v - u)^T Tau^{-1} (v - u) / 2).
 // One CTA per cell (persistent over cells); thread 0 forms Tau^{-1} and the
-// coefficients.  Every thread streams four consecutive values of a row (v2
+// coefficients.  Every thread streams eight consecutive values of a row (v2
 // varies), where the exponent is quadratic in the index: one exponential for
 // the first value and a multiplicative step whose ratio factors are tabulated
 // per cell (v2) and per row (N + N^2 exponentials per cell, in shared memory),
@@ -97,15 +97,18 @@ __global__ void __launch_bounds__(kEsThreads) esbgk_kernel(EsArgs a) {
   using V = Quad4<Tio>;
   __shared__ EsCell sc;
   // Along a row (w0, w1 fixed) the exponent is q(w2) = A w2^2 + 2 B w2 + C, A = Tinv_zz,
-  // B = Tinv_xz w0 + Tinv_yz w1.  Each group of four starts from E = exp(-q/2) (<= 1) and steps
+  // B = Tinv_xz w0 + Tinv_yz w1.  Each group of eight starts from E = exp(-q/2) (<= 1) and steps
   // with E_{j+1} = E_j U[j] W[row]: U[j] = exp(-A h w2_j) (per cell), W = exp(-(A h^2 + 2 B h)/2)
   // (per row).  Every factor is a bounded exponential (|A h w2| <= A h L, |B h| <= 2 A' h L), so
-  // nothing overflows however far the grid reaches into the Gaussian's tails.
+  // nothing overflows however far the grid reaches into the Gaussian's tails.  Groups of eight
+  // values per exponential: seven steps add at most seven roundings to E.  A group whose first
+  // value is below 1e-280 (a narrow Gaussian whose peak lies further along the group) takes one
+  // exponential per value, like a group with a ratio outside (1e-300, 1e300).
   extern __shared__ double tabs[];
   double* U = tabs;
   double* Wr = tabs + N;
   constexpr int n3 = N * N * N, nq = n3 / 4;
-  static_assert(N % 4 == 0, "row segments of four");
+  static_assert(N % 8 == 0, "row segments of eight");
   const double h = 2.0 * a.L / N;
   for (long long c = blockIdx.x; c < a.n_cells; c += gridDim.x) {
     __syncthreads();
@@ -128,24 +131,25 @@ __global__ void __launch_bounds__(kEsThreads) esbgk_kernel(EsArgs a) {
     }
     __syncthreads();
     const size_t base = size_t(c) * nq;
-    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-      const int idx = 4 * q, row = idx / N, j0 = row / N, j1 = row % N, j2 = idx % N;
+    for (int q2 = threadIdx.x; q2 < nq / 2; q2 += blockDim.x) {
+      const int idx = 8 * q2, row = idx / N, j0 = row / N, j1 = row % N, j2 = idx % N;
       const double w0 = -a.L + j0 * h - e.u[0], w1 = -a.L + j1 * h - e.u[1], w2 = -a.L + j2 * h - e.u[2];
       const double B = e.Li[4] * w0 + e.Li[5] * w1;
       const double C = e.Li[0] * w0 * w0 + 2.0 * e.Li[3] * w0 * w1 + e.Li[1] * w1 * w1;
       double E = exp(-0.5 * ((A * w2 + 2.0 * B) * w2 + C));
       const double wr = Wr[row];
-      double rs[3];
-      bool step = true;
+      double rs[7];
+      bool step = E > 1e-280;                 // a subnormal start would lose the group's precision
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
+      for (int k = 0; k < 7; ++k) {
         rs[k] = U[j2 + k] * wr;
         step &= rs[k] > 1e-300 && rs[k] < 1e300;
       }
-      double f[4], o[4];
-      V::ld(a.f, base + q, f);
+      double f[8], o[8];
+      V::ld(a.f, base + 2 * q2, *reinterpret_cast<double(*)[4]>(f));
+      V::ld(a.f, base + 2 * q2 + 1, *reinterpret_cast<double(*)[4]>(f + 4));
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < 8; ++k) {
         if (k > 0) {
           if (step) {
             E *= rs[k - 1];
@@ -156,7 +160,8 @@ __global__ void __launch_bounds__(kEsThreads) esbgk_kernel(EsArgs a) {
         }
         o[k] = fma(e.cg, E, e.cf * f[k]);
       }
-      V::st(a.out, base + q, o);
+      V::st(a.out, base + 2 * q2, *reinterpret_cast<const double(*)[4]>(o));
+      V::st(a.out, base + 2 * q2 + 1, *reinterpret_cast<const double(*)[4]>(o + 4));
     }
   }
 }
