@@ -746,6 +746,15 @@ def run_ours(args, rank, world, local_rank):
                     "frac": (mom_bytes / (mom_ms / 1e3) / 1e9 / peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None,
                     "bytes_per_launch": mom_bytes, "bound": "hbm", "traffic": load_traffic("moments_f64")},
     }
+    if world > 1:
+        # replicas: the single-GPU sub-measurements below (next rows, comparisons, serving,
+        # CPU baseline) belong to the 1-GPU run; the other GPUs are not held for them
+        print(json.dumps(line), flush=True)
+        plan.close()
+        plan32.close()
+        planx.close()
+        planm.close()
+        return
     # regime update on the 2D grid (indicators + Algorithm 1): the 256 x 256 spatial grid of
     # the ragged workload, and a 4096 x 4096 grid (inputs > L2) for the throughput and roofline
     t256 = time_regime(torch, coll, synth, dev, 256, 256, 50)
