@@ -109,3 +109,24 @@ def test_time_order_against_rk4(cell):
     assert all(1.6 < r < 2.5 for r in r1), (err1, r1)
     assert all(3.2 < r < 5.0 for r in r2), (err2, r2)
     assert err2[-1] < err1[-1]
+
+
+def test_asymptotic_preserving_limit(cell):
+    """sec. 4.4: the penalised step stays bounded as eps -> 0 (no 1/eps blow-up) and
+    tends to the limit of its implicit equation, beta1 (M1 - f1) = -(Q(f) - beta0 (M0 - f)),
+    i.e. f1 -> M1 + (Q(f) - beta0 (M0 - f)) / beta1, with an O(eps) remainder."""
+    m = mom(cell)
+    r = np.random.default_rng(5)
+    tr = 0.05 * cell * r.uniform(-1, 1, cell.shape)
+    m1 = mom(cell - 0.05 * tr)
+    M0, b0 = imex.maxwellian(*m, N, L), imex.beta(m[0])
+    M1, b1 = imex.maxwellian(*m1, N, L), imex.beta(m1[0])
+    q = Q(cell)
+    limit = M1 + (q - b0 * (M0 - cell)) / b1
+    errs = []
+    for eps in (1e-2, 1e-4, 1e-6):
+        f1 = imex.first_order(cell, q, m, 0.05, eps, L, tr=tr, mom1=m1)
+        assert np.abs(f1).max() < 10.0 * np.abs(limit).max()
+        errs.append(rel(f1, limit))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-5
+    assert errs[1] / errs[2] > 50.0                          # first order in eps

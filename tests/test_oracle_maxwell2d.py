@@ -122,3 +122,34 @@ def test_grid_symmetries_and_scaling():
     assert np.max(np.abs(m2.q_fast(refl1(f), p) - refl1(Q))) < 1e-13 * scale
     assert np.max(np.abs(m2.q_fast(rot90(f), p) - rot90(Q))) < 1e-13 * scale
     assert np.max(np.abs(m2.q_fast(2.0 * f, p) - 4.0 * Q)) < 1e-13 * scale
+
+
+def test_entropy_dissipation_2d():
+    """H-theorem in 2D: sum Q log f < 0 for two separated Maxwellians plus a broad floor."""
+    p = m2.Params2D(N=32, L=8.0, A=16)
+    D = []
+    for s in (0.5, 1.0, 1.5):
+        f = m2.maxwellian(p, 1.0, (s, 0.0), 1.0) + m2.maxwellian(p, 0.5, (-s, 0.0), 0.7) + \
+            1e-3 * m2.maxwellian(p, 1.0, (0.0, 0.0), 5.0)
+        Q = m2.q_fast(f, p)
+        D.append(float((Q * np.log(f)).sum()))
+        assert D[-1] < 0
+    assert D[0] > D[1] > D[2]
+
+
+def test_support_growth_bound_2d():
+    """Q of a bump supported in radius S lives in radius sqrt(2) S up to spectral error,
+    which falls as N grows (truncation R = 2S, L = (3 + sqrt 2) S / 2)."""
+    S = 3.0
+    L = (3.0 + math.sqrt(2.0)) * S / 2.0
+    ratios = []
+    for N in (16, 32, 64):
+        p = m2.Params2D(N=N, L=L, S=S, A=N)
+        x = m2.grid(p)
+        V = np.sqrt(x[:, None] ** 2 + x[None, :] ** 2)
+        r = V / S
+        f = np.where(r < 1.0, np.exp(-1.0 / np.maximum(1e-300, 1.0 - r * r)), 0.0)
+        Q = m2.q_fast(f, p)
+        out = V > math.sqrt(2.0) * S
+        ratios.append(float(np.abs(Q[out]).max() / np.abs(Q[~out]).max()))
+    assert ratios[0] > ratios[1] > ratios[2] and ratios[2] < 2e-3, ratios
