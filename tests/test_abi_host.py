@@ -95,3 +95,50 @@ def test_m2d_reject_bad_desc():
         with pytest.raises(coll.CollError) as e:
             coll.coll_m2d_tables_host(coll.make_m2d_desc(**kw))
         assert e.value.status == coll.COLL_EINVAL
+
+
+def test_argument_errors_without_a_gpu():
+    """Every entry point rejects bad arguments on the host, before any CUDA call, and
+    empty batches are no-ops (COLL_OK) that touch nothing."""
+    import ctypes
+    lib, E, OK = coll._lib, coll.COLL_EINVAL, coll.COLL_OK
+    out = ctypes.c_void_p()
+    assert lib.coll_plan_create(None, ctypes.byref(out)) == E
+    assert lib.coll_plan_destroy(None) == E
+    assert lib.coll_eval_batch(None, None, None, 1, None, 0, None) == E
+    assert lib.coll_plan_set_variant(None, 0) == E
+    assert lib.coll_device_status(None) == E
+    assert lib.coll_device_status_clear(None) == E
+    assert lib.coll_m2d_plan_create(None, ctypes.byref(out)) == E
+    assert lib.coll_m2d_plan_destroy(None) == E
+    assert lib.coll_m2d_eval_batch(None, None, None, 1, None) == E
+    assert lib.coll_m2d_device_status(None) == E
+    bad2d = coll.make_m2d_desc(16, 8.0, A=5000)
+    assert lib.coll_m2d_plan_create(ctypes.byref(bad2d), ctypes.byref(out)) == E
+    # moments: odd N, negative count, bad io type; zero cells is a no-op
+    assert lib.moments_realizability(None, 0, 15, 8.0, 1, 1e-3, 1e-4, None, None, None) == E
+    assert lib.moments_realizability(None, 0, 16, 8.0, -1, 1e-3, 1e-4, None, None, None) == E
+    assert lib.moments_realizability(None, 2, 16, 8.0, 1, 1e-3, 1e-4, None, None, None) == E
+    assert lib.moments_realizability(None, 0, 16, 8.0, 0, 1e-3, 1e-4, None, None, None) == OK
+    assert lib.moments_realizability(None, 0, 16, 8.0, 1, 1e-3, 1e-4, None, None, None) == E
+    # regime: missing parameters, non-positive spacing, empty grid, missing arrays
+    p = coll.coll_regime_params(1e-4, 1.0, 1.0, 1.0 / 256, 1.0 / 256, 1e-3, 2.8e-5, 1e-4)
+    assert lib.regime_update(None, None, None, 4, 4, None, None, None, None) == E
+    bad = coll.coll_regime_params(1e-4, 1.0, 1.0, 0.0, 1.0 / 256, 1e-3, 2.8e-5, 1e-4)
+    assert lib.regime_update(None, None, None, 4, 4, ctypes.byref(bad), None, None, None) == E
+    assert lib.regime_update(None, None, None, 0, 4, ctypes.byref(p), None, None, None) == OK
+    assert lib.regime_update(None, None, None, 4, 4, ctypes.byref(p), None, None, None) == E
+    # IMEX: stage out of range, eps <= 0, unsupported N, missing inputs of the stage
+    assert lib.coll_imex_stage(7, None, None, None, None, None, None, None, 0, 16, 8.0, 1, 0.1, 1.0, None, None) == E
+    assert lib.coll_imex_stage(1, None, None, None, None, None, None, None, 0, 16, 8.0, 1, 0.1, 0.0, None, None) == E
+    assert lib.coll_imex_stage(1, None, None, None, None, None, None, None, 0, 20, 8.0, 1, 0.1, 1.0, None, None) == \
+        coll.COLL_EUNSUPPORTED
+    assert lib.coll_imex_stage(2, None, None, None, None, None, None, None, 0, 16, 8.0, 1, 0.1, 1.0, None, None) == E
+    assert lib.coll_imex_stage(2, None, None, None, None, None, None, None, 0, 16, 8.0, 0, 0.1, 1.0, None, None) == OK
+    # ES-BGK: beta >= 1, mu0 <= 0, eps <= 0
+    for beta, mu0, eps in ((1.0, 1.0, 1.0), (-0.5, 0.0, 1.0), (-0.5, 1.0, -1.0)):
+        assert lib.coll_esbgk_step(None, None, 0, 16, 8.0, 1, 0.1, eps, beta, mu0, None, None) == E
+    assert lib.coll_advance(None, None, 1, 0.1, 0, None) == E
+    nb = ctypes.c_size_t()
+    assert lib.coll_ragged_workspace_size(None, None, 1, ctypes.byref(nb)) == E
+    assert lib.coll_eval_ragged(None, None, 0, None, 0, None) == E
