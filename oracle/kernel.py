@@ -35,7 +35,7 @@ from .quadrature import gauss_legendre, hemisphere_rule
 
 @dataclass(frozen=True)
 class Params:
-    """Operator and grid parameters (names follow the paper / SURVEY notation)."""
+    """Operator and grid parameters (names follow the paper's notation, sec. 2.1 and 4.4.1)."""
     N: int
     L: float
     S: float = 0.0            # support radius; 0 -> 2L/(3+sqrt 2); truncation R = 2S

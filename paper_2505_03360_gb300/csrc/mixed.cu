@@ -140,6 +140,7 @@ __device__ int g_mix_drop_commit = 0;
 
 struct MixShared {
   uint64_t bar[kMixMaxWG];
+  uint64_t tbar[kMixMaxWG];   // teardown: one fresh commit per warpgroup after an expired wait
   uint32_t tbase;
   int abort;
   int drop_commit;
@@ -420,8 +421,10 @@ __global__ void __launch_bounds__(MixCfg<N, P>::THREADS, 1) mixed_kernel(CollArg
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int w = 0; w < C::WG; ++w)
+    for (int w = 0; w < C::WG; ++w) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&sh.bar[w])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&sh.tbar[w])), "r"(1));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     sh.abort = 0;
     sh.drop_commit = g_mix_drop_commit;
@@ -445,8 +448,15 @@ __global__ void __launch_bounds__(MixCfg<N, P>::THREADS, 1) mixed_kernel(CollArg
     if (MixCell<N, Tio, P>::cell(f, Q, tab, tmax, a.n_terms, ws, sm + C::B_SETS + wg * C::A_TILE, abase, bbase, tacc, tG, phase, pending, sh, bad))
       break;
   }
-  // a wait that expired may leave this warpgroup's last MMA batch in flight
-  if (pending) (void)wait_parity(&sh.bar[wg], phase);
+  // A wait that expired may leave this warpgroup's last MMA batch in flight,
+  // and its own completion signal may never come.  A fresh commit from the
+  // issuing thread to a barrier of its own arrives once every MMA that thread
+  // started has completed; tensor memory is freed only after that arrival
+  // (bounded wait).
+  if (pending) {
+    if ((tid & 127) == 0) mma_commit(&sh.tbar[wg]);
+    (void)wait_parity(&sh.tbar[wg], 0);
+  }
   fence_before();
   if (__syncthreads_or(bad) && tid == 0) atomicOr(a.status, kStatusNonFinite);
   if (sh.abort && tid == 0) atomicOr(a.status, kStatusTimeout);

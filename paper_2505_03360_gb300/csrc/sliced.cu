@@ -173,6 +173,7 @@ enum SlPass : int { kSF2 = 0, kSF1, kSF0, kSX, kSY, kSZ };
 
 struct SlShared {
   uint64_t bar[kSlMaxWG];
+  uint64_t tbar[kSlMaxWG];   // teardown: one fresh commit per warpgroup after an expired wait
   uint32_t tbase;
   uint32_t abort;       // set in both CTAs of the cluster by a warpgroup whose wait expired
   float mx[3];          // [0], [1]: maximum modulus of the current / next pass input; [2]: max (|Re F| + |Im F|)
@@ -547,8 +548,10 @@ __global__ void __launch_bounds__(SlCfg<N>::THREADS, 1) sliced_kernel(CollArgs a
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int w = 0; w < C::WG; ++w)
+    for (int w = 0; w < C::WG; ++w) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&sh.bar[w])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&sh.tbar[w])), "r"(1));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     sh.abort = 0u;
   }
@@ -573,8 +576,14 @@ __global__ void __launch_bounds__(SlCfg<N>::THREADS, 1) sliced_kernel(CollArgs a
                              phase, pending, sh, bad))
       break;
   }
-  // a wait that expired may leave this warpgroup's last MMA batch in flight
-  if (pending) (void)wait_parity(&sh.bar[wg], phase);
+  // A wait that expired may leave this warpgroup's last MMA batch in flight.
+  // A fresh commit from the issuing thread to a barrier of its own arrives once
+  // every MMA that thread started has completed; tensor memory is freed only
+  // after that arrival (bounded wait).
+  if (pending) {
+    if ((tid & 127) == 0) mma_commit(&sh.tbar[wg]);
+    (void)wait_parity(&sh.tbar[wg], 0);
+  }
   fence_before();
   if (__syncthreads_or(bad) && tid == 0) atomicOr(a.status, kStatusNonFinite);
   if (sh.abort && tid == 0) atomicOr(a.status, kStatusTimeout);

@@ -36,7 +36,10 @@ cudaError_t scratch_address(int dev, void** out) {
   if (!g_scratch_ready[dev].load(std::memory_order_relaxed)) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || p == nullptr) return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+    if (e != cudaSuccess || p == nullptr) {
+      (void)cudaGetLastError();   // not left behind for the next launch check to report
+      return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+    }
     g_scratch_ptr[dev] = p;
     g_scratch_ready[dev].store(true, std::memory_order_release);
   }
