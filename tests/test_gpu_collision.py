@@ -206,3 +206,26 @@ def test_slab_shape_variants_and_autotune(prec, N):
     torch.cuda.synchronize()
     assert torch.equal(Q, outs[chosen])
     plan.close()
+
+
+def test_fp64_maxwell_molecules_N32_against_oracle():
+    """lambda = 0 at N = 32 (M = 48, Mr = 8: 192 gain terms, Psi tabulated per
+    radial node), the Maxwell-molecule plan the serving workload uses, per cell
+    against the oracle at the FP64 tolerance; the batch spans several CTAs."""
+    f = synth.bimodal_batch(3, 32, L_CFG, seed=synth.BASE_SEED + 31)
+    check_cells(f, "f64", N=32, L=L_CFG, lam=0.0, M=48, Mtheta=4, Mr=8)
+
+
+@pytest.mark.parametrize("N", [48, 64])
+def test_fp32_maxwell_molecules_large_grids_sampled(N):
+    """lambda = 0 at N = 48 and 64 in FP32 (the serving workload's largest
+    grids): a batch larger than one CTA round, one sampled cell against the
+    oracle (multipliers generated per direction) at the FP32 tolerance."""
+    from oracle.collision import q_fast_streaming
+    n = 5
+    f = synth.bimodal_batch(n, N, L_CFG, seed=synth.BASE_SEED + 40 + N).astype(np.float32)
+    Qg = run_gpu(f, "f32", N=N, L=L_CFG, lam=0.0, M=48, Mtheta=4, Mr=8)
+    p = Params(N=N, L=L_CFG, lam=0.0, M=48, Mtheta=4, Mr=8)
+    c = n - 1
+    want = q_fast_streaming(f[c].astype(np.float64), p)
+    assert rel(Qg[c], want) <= TOL["f32"], rel(Qg[c], want)

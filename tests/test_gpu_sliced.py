@@ -139,3 +139,22 @@ def test_sliced_full_batch_config3():
         assert rel(qs[c].cpu().numpy(), q_fast(fnp[c], pr, m)) <= TOL, c
     ps.close()
     p64.close()
+
+
+@pytest.mark.parametrize("N", [16, 32])
+def test_sliced_maxwell_molecules_against_oracle(N):
+    """lambda = 0 (Mr = 8 radial nodes per direction: 128 or 192 gain terms)
+    per cell against the oracle, not only against the FP64 GPU path."""
+    M = 32 if N == 16 else 48
+    cells = synth.bimodal_batch(3, N, L, seed=synth.BASE_SEED + 50 + N)
+    f = torch.from_numpy(cells).cuda()
+    p = coll.Plan(N, L, lam=0.0, M=M, Mtheta=4, Mr=8, prec="mixed_sliced", max_cells=len(cells))
+    Q = p.eval(f)
+    torch.cuda.synchronize()
+    assert p.status() == coll.COLL_OK
+    pr = Params(N=N, L=L, lam=0.0, M=M, Mtheta=4, Mr=8)
+    m = multipliers(pr)
+    for c in range(len(cells)):
+        err = rel(Q[c].cpu().numpy(), q_fast(cells[c], pr, m))
+        assert err <= TOL, (c, err)
+    p.close()

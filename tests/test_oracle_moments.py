@@ -101,12 +101,16 @@ def test_P9_mixture_moments_analytic(seed):
 
 def _l1_resolution(f, L):
     """Bound on the fixed-point L1 distance's error: f and M are integers in
-    units of 2^-P2 with P2 = L1_TOP - (exponent of the larger peak), each
-    point off by < 2 units (truncated f, rounded M, rounded amplitude), over
-    at most N^3 points of volume h^3."""
+    units of 2^-P2 with P2 = L1_TOP - (exponent of the larger peak).  Per
+    point: truncating f loses < 1 unit; M_fix = round(A_fix E / 2^31) is off by
+    <= 1/2 (final rounding) + 1/2 E / 2^31 (rounded amplitude, E < 2^31) +
+    1/2 A_fix / 2^31 (rounded 1D factor, A_fix < 2^30), i.e. < 1.25 units, plus
+    the exponential's and the amplitude's relative rounding (far below a
+    unit).  So < 2.25 units per point (2.5 taken) over at most N^3 points of
+    volume h^3."""
     peak = 2.0 * float(np.abs(f).max())          # the Maxwellian's peak stays within 2x of f's for these cases
     P2 = om.L1_TOP - math.frexp(peak)[1]
-    return 2.0 * 2.0 ** -P2 * (2 * L) ** 3
+    return 2.5 * 2.0 ** -P2 * (2 * L) ** 3
 
 
 def test_P9_maxwellian_special_case():
@@ -239,3 +243,37 @@ def test_float32_input_is_exact_widening():
     a, ma = om.cell_moments(f, L, 1e-3, 1e-4)
     b, mb = om.cell_moments(f.astype(np.float64), L, 1e-3, 1e-4)
     assert ma == mb and np.array_equal(om.pack(a), om.pack(b))
+
+
+def test_l1_fixed_point_band_against_plain_sum():
+    """The fixed-point L1 distance (reading of sec. 3.3, which fixes no
+    precision) against the plain definition sum |f - M_{rho,u,T}| dv^3 in
+    float64 with numpy's exp, on bench-shaped bimodal cells (N = 32,
+    L = 13.24) and on near-equilibrium cells whose distance lies near the
+    default delta0 = 1e-4.  Each difference is within the worst-case bound;
+    the measured band is below 2e-3 delta0 (largest seen: 1.4e-3 delta0), so a
+    cell's bit2 can differ from the real-number test only if its distance is
+    within 2e-7 of delta0."""
+    N, L, delta0 = 32, synth.DEFAULT_L, 1e-4
+    cells = [synth.bimodal_batch(6, N, L, seed=synth.BASE_SEED + 2)]
+    r = np.random.default_rng(5)
+    near = []
+    for _ in range(6):
+        rho, u, T = r.uniform(0.5, 2), r.uniform(-1.5, 1.5, 3), r.uniform(0.5, 2)
+        eps = 10 ** r.uniform(-5, -3)
+        near.append(synth.maxwellian_cells(N, L, [rho * (1 - eps), rho * eps], [u, u + r.uniform(-1, 1, 3)],
+                                           [T, T * r.uniform(0.5, 2)]).sum(0))
+    cells.append(np.stack(near))
+    f = np.concatenate(cells)
+    dv3 = (2 * L / N) ** 3
+    band = 0.0
+    for c in range(f.shape[0]):
+        out, mask = om.cell_moments(f[c], L, 1e-3, delta0)
+        M = synth.maxwellian_cells(N, L, [out["rho"]], [out["u"]], [out["T"]])[0]
+        plain = float(np.abs(f[c] - M).sum() * dv3)
+        diff = abs(out["l1"] - plain)
+        assert diff < _l1_resolution(f[c], L), c
+        band = max(band, diff)
+        if abs(plain - delta0) > 2e-3 * delta0:
+            assert bool(mask & 4) == (plain > delta0), c
+    assert band < 2e-3 * delta0, band
