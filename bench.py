@@ -476,6 +476,7 @@ def run_ours(args, rank, world, local_rank):
     ws = plan.reserve(n)
     mom = torch.empty((n, coll.MOMENT_DOUBLES), dtype=torch.float64, device=dev)
     mask = torch.empty((n,), dtype=torch.uint8, device=dev)
+    cons = torch.empty((n, 8), dtype=torch.float64, device=dev)
     stream = torch.cuda.Stream(device=dev)
 
     def step(ev=None):
@@ -488,6 +489,10 @@ def run_ours(args, rank, world, local_rank):
                                    mom, mask, stream=stream)
         if ev is not None:
             ev[2].record(stream)
+        # FP64 conservation check of Q (mass, momentum, energy per cell)
+        coll.coll_conservation(Q, 0 if Q.dtype == torch.float64 else 1, N, w["L"], n, cons, stream=stream)
+        if ev is not None:
+            ev[3].record(stream)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -495,7 +500,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
-    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(args.steps)]
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(4)) for _ in range(args.steps)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = coll.coll_launch_count()
     with ClockSampler(_smi_id(torch, dev, local_rank)) as clk:
@@ -507,8 +512,9 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize(dev)
     launches = coll.coll_launch_count() - launches0
     elapsed = t_start.elapsed_time(t_end) / 1e3
-    coll_ms = sum(a.elapsed_time(b) for a, b, _ in evs) / args.steps
-    mom_ms = sum(b.elapsed_time(c) for _, b, c in evs) / args.steps
+    coll_ms = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
+    mom_ms = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps
+    cons_ms = sum(e[2].elapsed_time(e[3]) for e in evs) / args.steps
     assert plan.status() == coll.COLL_OK
     if world > 1:
         elapsed = max_over_ranks(elapsed, world, device=dev)
@@ -527,6 +533,8 @@ def run_ours(args, rank, world, local_rank):
     e2e_steps = max(3, min(args.steps, 4))
     fb, Qb = [f, torch.empty_like(f)], [Q, torch.empty_like(Q)]
     momb, maskb = [mom, torch.empty_like(mom)], [mask, torch.empty_like(mask)]
+    consb = [cons, torch.empty_like(cons)]
+    cons_pin = [torch.empty(cons.shape, dtype=cons.dtype).pin_memory() for _ in range(2)]
     Q_pin = [torch.empty(Q.shape, dtype=Q.dtype).pin_memory() for _ in range(2)]
     mom_pin = [torch.empty(mom.shape, dtype=mom.dtype).pin_memory() for _ in range(2)]
     mask_pin = [torch.empty(mask.shape, dtype=mask.dtype).pin_memory() for _ in range(2)]
@@ -549,6 +557,7 @@ def run_ours(args, rank, world, local_rank):
             coll.coll_eval_batch(plan.handle, fb[b], Qb[b], n, ws, stream=stream)
             coll.moments_realizability(fb[b], io, N, w["L"], n, w["eta0"], w["delta0"], momb[b], maskb[b],
                                        stream=stream)
+            coll.coll_conservation(Qb[b], io, N, w["L"], n, consb[b], stream=stream)
             ev_comp[b] = torch.cuda.Event()
             ev_comp[b].record(stream)
             s_out.wait_event(ev_comp[b])
@@ -556,6 +565,7 @@ def run_ours(args, rank, world, local_rank):
                 Q_pin[b].copy_(Qb[b], non_blocking=True)
                 mom_pin[b].copy_(momb[b], non_blocking=True)
                 mask_pin[b].copy_(maskb[b], non_blocking=True)
+                cons_pin[b].copy_(consb[b], non_blocking=True)
             ev_out[b] = torch.cuda.Event()
             ev_out[b].record(s_out)
 
@@ -571,7 +581,16 @@ def run_ours(args, rank, world, local_rank):
     e2e_s = e0.elapsed_time(e1) / 1e3
     e2e_s = max_over_ranks(e2e_s, world, device=dev)
     assert bool(torch.equal(Q_pin[(e2e_steps - 1) % 2], Qb[(e2e_steps - 1) % 2].cpu()))
-    del fb[1], Qb[1], momb[1], maskb[1], Q_pin, mom_pin, mask_pin
+    del fb[1], Qb[1], momb[1], maskb[1], consb[1], Q_pin, mom_pin, mask_pin, cons_pin
+
+    def cons_errors(Qv):
+        """Largest relative mass, momentum and energy errors over the batch (coll_conservation)."""
+        inv = coll.conservation(Qv, w["L"], stream=stream)
+        torch.cuda.synchronize(dev)
+        e = coll.conservation_errors(inv)
+        return {"mass": float(e[:, 0].max()), "momentum": float(e[:, 1].max()), "energy": float(e[:, 2].max())}
+
+    cons64 = cons_errors(Q)
 
     # float-pair variant (FP64-class accuracy on the FP32 pipe) on the same cells
     Qx = torch.empty_like(f)
@@ -590,6 +609,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     tx = ax.elapsed_time(bx) / 1e3 / args.steps
     errx = float(torch.linalg.vector_norm(Qx - Q) / torch.linalg.vector_norm(Q))
+    consx = cons_errors(Qx)
     del Qx
 
     # FP32 variant on the same cells (reported beside the FP64 line)
@@ -610,6 +630,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     t32 = a32.elapsed_time(b32) / 1e3 / args.steps
     err32 = float(torch.linalg.vector_norm(Q32.double() - Q) / torch.linalg.vector_norm(Q))
+    cons32 = cons_errors(Q32)
     del Q32, f32
 
     # tensor-core DFT-GEMM variant (f16 hi+lo split, FP32 accumulate) on the same FP64 cells
@@ -631,6 +652,7 @@ def run_ours(args, rank, world, local_rank):
     assert planm.status() == coll.COLL_OK
     cell_err = torch.linalg.vector_norm((Qm - Q).reshape(n, -1), dim=1) / torch.linalg.vector_norm(Q.reshape(n, -1), dim=1)
     errm = float(torch.linalg.vector_norm(Qm - Q) / torch.linalg.vector_norm(Q))
+    consm = cons_errors(Qm)
     # bf16 three-part variant on the same cells
     planb = coll.Plan(N, w["L"], lam=w["lam"], M=w["M"], Mtheta=w["Mtheta"], Mr=w["Mr"], prec="mixed_bf16x3",
                       io_dtype=0, max_cells=n, device=dev)
@@ -648,6 +670,7 @@ def run_ours(args, rank, world, local_rank):
     assert planb.status() == coll.COLL_OK
     cell_errb = torch.linalg.vector_norm((Qm - Q).reshape(n, -1), dim=1) / torch.linalg.vector_norm(Q.reshape(n, -1), dim=1)
     errb = float(torch.linalg.vector_norm(Qm - Q) / torch.linalg.vector_norm(Q))
+    consb_ = cons_errors(Qm)
     planb.close()
     # fixed-point-slice tensor-core variant (exact leading products, float-pair intermediates)
     plans = coll.Plan(N, w["L"], lam=w["lam"], M=w["M"], Mtheta=w["Mtheta"], Mr=w["Mr"], prec="mixed_sliced",
@@ -666,6 +689,7 @@ def run_ours(args, rank, world, local_rank):
     assert plans.status() == coll.COLL_OK
     cell_errs = torch.linalg.vector_norm((Qm - Q).reshape(n, -1), dim=1) / torch.linalg.vector_norm(Q.reshape(n, -1), dim=1)
     errs = float(torch.linalg.vector_norm(Qm - Q) / torch.linalg.vector_norm(Q))
+    conss = cons_errors(Qm)
     n_terms_s = plans.n_terms
     plans.close()
     del Qm
@@ -684,14 +708,15 @@ def run_ours(args, rank, world, local_rank):
     tc_peak = peaks.get("bf16_tflops")
     mma_flops = mixed_mma_flops_per_cell(N, planm.n_terms) * n
     mom_bytes = f.numel() * 8 + mom.numel() * 8 + mask.numel()
+    cons_bytes = Q.numel() * 8 + cons.numel() * 8
     e2e_bytes_in = f.numel() * 8
-    e2e_bytes_out = Q.numel() * 8 + mom.numel() * 8 + mask.numel()
+    e2e_bytes_out = Q.numel() * 8 + mom.numel() * 8 + mask.numel() + cons.numel() * 8
     line = {
         "metric": METRIC, "value": value, "unit": "cell-evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "4096-cell batch, N=32^3, hard spheres (lambda=1), M=48 (24 hemisphere directions), "
-                               "Mr=16, FP64 collision + FP64 moments/realizability mask (eta0=1e-3, delta0=1e-4)",
+                               "Mr=16, FP64 collision + FP64 moments/realizability mask (eta0=1e-3, delta0=1e-4) + FP64 conservation check of Q",
                    "global_batch": n * world, "seq_len": N ** 3, "parallelism": "replicas x%d" % world,
                    "l2": "inputs larger than L2 (f and Q are 1.07 GB each)"},
         "e2e": {"value": whole_job_rate(n * e2e_steps, world, e2e_s), "unit": "cell-evals/s",
@@ -706,13 +731,15 @@ def run_ours(args, rank, world, local_rank):
                      "flops_per_launch": flops, "ms_per_launch": coll_ms},
         "clocks": clocks,
         "variants": {"f32x2": {"value": n / tx, "unit": "cell-evals/s", "rel_l2_vs_f64": errx,
-                               "ms_per_launch": 1e3 * tx, "arithmetic": "float pairs (~48 bits) on the FP32 pipe"},
+                               "ms_per_launch": 1e3 * tx, "arithmetic": "float pairs (~48 bits) on the FP32 pipe",
+                               "conservation_rel_max": consx},
                      "f32": {"value": n / t32, "unit": "cell-evals/s", "rel_l2_vs_f64": err32,
-                             "ms_per_launch": 1e3 * t32},
+                             "ms_per_launch": 1e3 * t32, "conservation_rel_max": cons32},
                      "mixed_f16x2": {
                          "value": n / tm, "unit": "cell-evals/s", "rel_l2_vs_f64": errm,
                          "cell_rel_l2_median": float(cell_err.median()), "cell_rel_l2_max": float(cell_err.max()),
                          "ms_per_launch": 1e3 * tm, "speedup_vs_f64": coll_ms / (1e3 * tm),
+                         "conservation_rel_max": consm,
                          "arithmetic": "DFT-GEMMs on tcgen05 tensor cores, f16 hi+lo operands, FP32 accumulate",
                          "roofline": {"bound": "tensor", "achieved": mma_flops / tm / 1e12, "peak": tc_peak,
                                       "unit": "TFLOP/s",
@@ -725,11 +752,13 @@ def run_ours(args, rank, world, local_rank):
                          "value": n / tb, "unit": "cell-evals/s", "rel_l2_vs_f64": errb,
                          "cell_rel_l2_median": float(cell_errb.median()), "cell_rel_l2_max": float(cell_errb.max()),
                          "ms_per_launch": 1e3 * tb, "speedup_vs_f64": coll_ms / (1e3 * tb),
+                         "conservation_rel_max": consb_,
                          "arithmetic": "DFT-GEMMs on tcgen05 tensor cores, bf16 hi+mid+lo operands, FP32 accumulate"},
                      "mixed_sliced": {
                          "value": n / ts, "unit": "cell-evals/s", "rel_l2_vs_f64": errs,
                          "cell_rel_l2_median": float(cell_errs.median()), "cell_rel_l2_max": float(cell_errs.max()),
                          "ms_per_launch": 1e3 * ts, "speedup_vs_f64": coll_ms / (1e3 * ts),
+                         "conservation_rel_max": conss,
                          "arithmetic": "DFT-GEMMs on tcgen05 tensor cores, fixed-point f16 slices (three 9-bit "
                                        "integer parts + f16 tail), two leading product levels summed exactly in "
                                        "FP32 tensor memory, float-pair intermediates",
@@ -745,6 +774,12 @@ def run_ours(args, rank, world, local_rank):
                     "achieved_gbs": mom_bytes / (mom_ms / 1e3) / 1e9, "peak_gbs": peaks.get("hbm_gbs"),
                     "frac": (mom_bytes / (mom_ms / 1e3) / 1e9 / peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None,
                     "bytes_per_launch": mom_bytes, "bound": "hbm", "traffic": load_traffic("moments_f64")},
+        "conservation": {"kernel": "cons_kernel<32, double> (exact fixed-point sums of Q (1, v, |v|^2) per cell)",
+                         "ms_per_launch": cons_ms, "achieved_gbs": cons_bytes / (cons_ms / 1e3) / 1e9,
+                         "peak_gbs": peaks.get("hbm_gbs"),
+                         "frac": (cons_bytes / (cons_ms / 1e3) / 1e9 / peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None,
+                         "bytes_per_launch": cons_bytes, "bound": "hbm",
+                         "rel_max_fp64": cons64},
     }
     if world > 1:
         # replicas: the single-GPU sub-measurements below (next rows, comparisons, serving,

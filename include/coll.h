@@ -245,6 +245,31 @@ coll_status moments_realizability(const void* f, int32_t io_dtype, int32_t N, do
                                   coll_moments* mom_out, uint8_t* mask_out, coll_stream stream);
 
 /*
+ * Collision invariants of Q, per cell (hypothesis H1, sec. 2: the collision
+ * operator preserves mass, momentum and kinetic energy, int Q dv = 0,
+ * int Q v dv = 0, int Q |v|^2 dv = 0; sec. 4.4.1: the truncated fast operator
+ * keeps mass exactly, momentum and energy to its accuracy).  For n_cells
+ * cells of N^3 values Q (io_dtype 0 = double, 1 = float; N in 16, 24, 32, 48,
+ * 64; the grid v = -L + j 2L/N of coll_eval_batch) it writes eight doubles per
+ * cell to out[c][0..7]:
+ *   m0 = int Q,  m1[d] = int Q v_d (d = 0, 1, 2),  m2 = int Q |v|^2,
+ *   a0 = int |Q|,  a1 = int |Q| (|v_0| + |v_1| + |v_2|),  a2 = int |Q| |v|^2,
+ * so |m0| / a0, max_d |m1[d]| / a1 and |m2| / a2 are relative conservation
+ * errors.  Every integral is an exact fixed-point sum (Q truncated to 2^-P,
+ * P = 61 - e with max |Q| < 2^e, times integer grid monomials, v = h k) rounded
+ * once to double and scaled by 2^-P h^3 (times h or h^2): bitwise reproducible
+ * and independent of launch shape and order.  A cell with a non-finite value
+ * gives eight NaN, an all-zero cell eight zeros.
+ *   Q    device, [n_cells][N][N][N], 16-byte aligned
+ *   out  device, [n_cells][8] doubles, caller-owned
+ * One kernel on stream; allocates nothing.  COLL_EINVAL for negative n_cells,
+ * a bad io_dtype or L, null or misaligned pointers; COLL_EUNSUPPORTED for
+ * other N; n_cells = 0 is a no-op.
+ */
+coll_status coll_conservation(const void* Q, int32_t io_dtype, int32_t N, double L, int64_t n_cells,
+                              double* out, coll_stream stream);
+
+/*
  * Regime update on the 2D spatial grid (sec. 4.5, Algorithm 1): per cell the
  * central-difference gradients and Laplacians of rho, u_x, u_y, T over the
  * one-cell stencil (sec. 4.5), the three eigenvalues of the 2D matrix

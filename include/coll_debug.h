@@ -39,9 +39,10 @@ coll_status coll_m2d_tables_host(const coll_m2d_plan_desc* desc, double* out, si
  * the tensor-core path (COLL_MIXED_F16X2).  With on != 0, in every later
  * launch warpgroup 0 of each CTA omits the completion signal of its first MMA
  * batch: its wait expires after about one second of SM clocks, the CTA stops,
- * waits (bounded) once more, frees its tensor memory and returns, and the
- * plan's sticky status reads COLL_ETIMEOUT (coll_device_status).  Nothing
- * faults or hangs; the launch takes about two seconds.  on = 0 restores normal
+ * waits (bounded) on a fresh completion signal for the MMAs it started, frees
+ * its tensor memory and returns, and the plan's sticky status reads
+ * COLL_ETIMEOUT (coll_device_status).  Nothing faults or hangs; the launch
+ * takes about one second.  on = 0 restores normal
  * operation.  Applies to the current device.  Returns COLL_ECUDA if the switch
  * cannot be written.
  */

@@ -73,6 +73,7 @@ def _load():
                                              ctypes.POINTER(SZ)]),
         "coll_eval_ragged": (I32, [ctypes.POINTER(coll_cell_group), ctypes.POINTER(I64), I32, P, SZ, P]),
         "moments_realizability": (I32, [P, I32, I32, D, I64, D, D, P, P, P]),
+        "coll_conservation": (I32, [P, I32, I32, D, I64, P, P]),
         "regime_update": (I32, [P, P, P, I32, I32, ctypes.POINTER(coll_regime_params), P, P, P]),
         "coll_imex_stage": (I32, [I32, P, P, P, P, P, P, P, I32, I32, D, I64, D, D, P, P]),
         "coll_esbgk_step": (I32, [P, P, I32, I32, D, I64, D, D, D, D, P, P]),
@@ -486,3 +487,28 @@ def moments(f, L, eta0=1e-3, delta0=1e-4, stream=None):
     mask = torch.empty((n,), dtype=torch.uint8, device=f.device)
     moments_realizability(f, io, N, L, n, eta0, delta0, mom, mask, stream=stream)
     return mom, mask
+
+
+def coll_conservation(Q, io_dtype: int, N: int, L: float, n_cells: int, out, stream=None, check=True) -> int:
+    st = _lib.coll_conservation(_ptr(Q), int(io_dtype), int(N), float(L), int(n_cells), _ptr(out),
+                                _stream_ptr(stream))
+    if check:
+        _check(st, "coll_conservation")
+    return st
+
+
+def conservation(Q, L, stream=None):
+    """Collision invariants [n, 8] (m0, m1[3], m2, a0, a1, a2; float64) of Q [n, N, N, N] on the device."""
+    import torch
+    n, N = Q.shape[0], Q.shape[-1]
+    io = 0 if Q.dtype == torch.float64 else 1
+    out = torch.empty((n, 8), dtype=torch.float64, device=Q.device)
+    coll_conservation(Q, io, N, L, n, out, stream=stream)
+    return out
+
+
+def conservation_errors(inv):
+    """[n, 3] relative errors |m0|/a0, max_d |m1_d|/a1, |m2|/a2 of coll_conservation records (torch)."""
+    import torch
+    return torch.stack([inv[:, 0].abs() / inv[:, 5], inv[:, 1:4].abs().amax(1) / inv[:, 6],
+                        inv[:, 4].abs() / inv[:, 7]], 1)

@@ -320,6 +320,17 @@ coll_status moments_realizability(const void* f, int32_t io_dtype, int32_t N, do
   return e == 0 ? COLL_OK : COLL_ECUDA;
 }
 
+coll_status coll_conservation(const void* Q, int32_t io_dtype, int32_t N, double L, int64_t n_cells, double* out,
+                              coll_stream stream) {
+  if (n_cells < 0 || (io_dtype != 0 && io_dtype != 1) || !(L > 0) || !std::isfinite(L)) return COLL_EINVAL;
+  if (N != 16 && N != 24 && N != 32 && N != 48 && N != 64) return COLL_EUNSUPPORTED;
+  if (n_cells == 0) return COLL_OK;
+  if (!Q || !out || (reinterpret_cast<uintptr_t>(Q) & 15u) != 0 || (reinterpret_cast<uintptr_t>(out) & 7u) != 0)
+    return COLL_EINVAL;
+  const int e = launch_conservation(Q, io_dtype == 0, N, L, n_cells, out, stream);
+  return e == 0 ? COLL_OK : COLL_ECUDA;
+}
+
 coll_status regime_update(const double* fields, const double* l1, const uint8_t* r_in, int32_t nx, int32_t ny,
                           const coll_regime_params* params, uint8_t* r_out, double* ind, coll_stream stream) {
   if (nx < 0 || ny < 0 || !params) return COLL_EINVAL;

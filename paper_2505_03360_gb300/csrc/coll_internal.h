@@ -126,6 +126,8 @@ int sliced_max_ctas_per_sm(int N, bool io_f64, int* ctas);
 // Moments kernel (moments.cu)
 int launch_moments(const void* f, int io_f64, int N, double L, long long n_cells, double eta0,
                    double delta0, coll_moments* mom, uint8_t* mask, void* stream);
+// Collision invariants of Q per cell (moments.cu)
+int launch_conservation(const void* Q, int io_f64, int N, double L, long long n_cells, double* out, void* stream);
 
 // Regime update on the 2D grid (regime.cu)
 int launch_regime(const double* fields, const double* l1, const uint8_t* r_in, int nx, int ny,

@@ -804,6 +804,89 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(int N, double L,
   mask[c] = mbits;
 }
 
+template <typename Tio>
+__device__ __forceinline__ void unpack16(const uint4 v, typename Bits<Tio>::U* b) {
+  if constexpr (sizeof(Tio) == 8) {
+    b[0] = (unsigned long long)v.x | ((unsigned long long)v.y << 32);
+    b[1] = (unsigned long long)v.z | ((unsigned long long)v.w << 32);
+  } else {
+    b[0] = v.x; b[1] = v.y; b[2] = v.z; b[3] = v.w;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Collision invariants of Q (hypothesis H1, sec. 2): per cell the exact
+// fixed-point sums of F = trunc(Q 2^P) times 1, k_d, |k|^2 and of |F| times
+// 1, |k_0| + |k_1| + |k_2|, |k|^2 (v = h k), each rounded once to double and
+// scaled by 2^-P h^3 (times h or h^2).  The same scale rule as the moment
+// sums: P = 61 - e with max |Q| < 2^e.  One CTA per cell, persistent: pass 0
+// takes max |Q| and finiteness, pass 1 (from L2) the eight sums.
+// ---------------------------------------------------------------------------
+struct ConsShared {
+  i128 red[(kMThreads / 32 + 1) * 8];
+  unsigned long long wmx[kMThreads / 32];
+  unsigned int wbad[kMThreads / 32];
+};
+
+// rows [row0, row0 + nrows) of a cell at base (shared or global memory)
+template <int N, typename Tio>
+__device__ __forceinline__ void cons_rows(const unsigned char* base, int row0, int nrows, int P, bool general,
+                                          i128 (&acc)[8]) {
+  using B = Bits<Tio>;
+  using U = typename B::U;
+  constexpr int half = N / 2;
+  constexpr int RB = N * int(sizeof(Tio)), NCH = RB / 16, EPC = 16 / int(sizeof(Tio));
+  constexpr int ROT = NCH < 8 ? NCH : 8;
+  const int s = threadIdx.x % ROT;
+  for (int lr = threadIdx.x; lr < nrows; lr += kMThreads) {
+    const int row = row0 + lr;
+    const long long k0 = row / N - half, k1 = row % N - half;
+    long long rl[3] = {0, 0, 0}, rh[3] = {0, 0, 0}, al[3] = {0, 0, 0}, ah[3] = {0, 0, 0};
+    const unsigned char* rp = base + size_t(lr) * RB;
+    auto add = [&](long long F, int k2) {
+      const long long aF = F < 0 ? -F : F;
+      const int flo = int(F & 0x7fffffffll), fhi = int(F >> 31);
+      const int alo = int(aF & 0x7fffffffll), ahi = int(aF >> 31);
+      const int ak = k2 < 0 ? -k2 : k2, k22 = k2 * k2;
+      rl[0] += flo; rh[0] += fhi;
+      rl[1] += (long long)flo * k2; rh[1] += (long long)fhi * k2;
+      rl[2] += (long long)flo * k22; rh[2] += (long long)fhi * k22;
+      al[0] += alo; ah[0] += ahi;
+      al[1] += (long long)alo * ak; ah[1] += (long long)ahi * ak;
+      al[2] += (long long)alo * k22; ah[2] += (long long)ahi * k22;
+    };
+    if (!general) {
+#pragma unroll
+      for (int i = 0; i < NCH; ++i) {
+        int j = i + s;
+        if (j >= NCH) j -= NCH;
+        U b[EPC];
+        unpack16<Tio>(*reinterpret_cast<const uint4*>(rp + 16 * j), b);
+#pragma unroll
+        for (int e = 0; e < EPC; ++e) add(B::fix(b[e], P), j * EPC + e - half);
+      }
+    } else {
+      const Tio* fr = reinterpret_cast<const Tio*>(rp);
+      for (int j2 = 0; j2 < N; ++j2) add(fix_val(fr[j2], P), j2 - half);
+    }
+    i128 R[3], A[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      R[c] = static_cast<i128>(rh[c]) * (static_cast<i128>(1) << 31) + static_cast<i128>(rl[c]);
+      A[c] = static_cast<i128>(ah[c]) * (static_cast<i128>(1) << 31) + static_cast<i128>(al[c]);
+    }
+    const long long r2 = k0 * k0 + k1 * k1, r1 = (k0 < 0 ? -k0 : k0) + (k1 < 0 ? -k1 : k1);
+    acc[0] += R[0];
+    acc[1] += R[0] * k0;
+    acc[2] += R[0] * k1;
+    acc[3] += R[1];
+    acc[4] += R[0] * r2 + R[2];
+    acc[5] += A[0];
+    acc[6] += A[0] * r1 + A[1];
+    acc[7] += A[0] * r2 + A[2];
+  }
+}
+
 int grid_for(const void* kernel, long long n_cells) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
@@ -812,6 +895,94 @@ int grid_for(const void* kernel, long long n_cells) {
   if (per < 1) per = 1;
   long long grid = static_cast<long long>(sms) * per;
   return int(grid > n_cells ? n_cells : grid);
+}
+
+template <int N, typename Tio>
+__global__ void __launch_bounds__(kMThreads, 4) cons_kernel(const Tio* __restrict__ Q, double L, long long n_cells,
+                                                           double* __restrict__ out) {
+  using B = Bits<Tio>;
+  using U = typename B::U;
+  constexpr int EPC = 16 / int(sizeof(Tio));
+  constexpr int BYTES = N * N * N * int(sizeof(Tio));
+  __shared__ ConsShared x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+  for (long long c = blockIdx.x; c < n_cells; c += gridDim.x) {
+    const unsigned char* base = reinterpret_cast<const unsigned char*>(Q + size_t(c) * N * N * N);
+    double* o = out + size_t(c) * 8;
+    // ---- pass 0: max |Q| (magnitude bits), finiteness
+    U mx = 0;
+    bool bad = false;
+    const uint4* s4 = reinterpret_cast<const uint4*>(base);
+    for (int i = tid; i < BYTES / 16; i += kMThreads) {
+      U e[EPC];
+      unpack16<Tio>(__ldg(s4 + i), e);
+#pragma unroll
+      for (int k = 0; k < EPC; ++k) {
+        const U a = e[k] & B::kAbs;
+        bad |= a >= B::kExp;
+        mx = a > mx ? a : mx;
+      }
+    }
+    mx = B::shfl_max(mx);
+    bad = __any_sync(0xffffffffu, bad);
+    __syncthreads();                                        // x.wmx may still be read for the previous cell
+    if (lane == 0) {
+      x.wmx[warp] = static_cast<unsigned long long>(__double_as_longlong(B::value(mx)));
+      x.wbad[warp] = bad ? 1u : 0u;
+    }
+    __syncthreads();
+    unsigned long long mxd = 0;
+    unsigned int fl = 0;
+#pragma unroll
+    for (int k = 0; k < kMThreads / 32; ++k) {
+      mxd = x.wmx[k] > mxd ? x.wmx[k] : mxd;
+      fl |= x.wbad[k];
+    }
+    const double qmax = __longlong_as_double(static_cast<long long>(mxd));
+    if (fl || qmax == 0.0) {                                // non-finite or all-zero cell
+      if (tid < 8) o[tid] = fl ? qnan : 0.0;
+      continue;
+    }
+    int e;
+    frexp(qmax, &e);
+    const bool general = e < (sizeof(Tio) == 8 ? -990 : -100);
+    const int P = kFixTop - e;
+    // ---- pass 1: the eight exact sums
+    i128 acc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = 0;
+    cons_rows<N, Tio>(base, 0, N * N, P, general, acc);
+    block_sum<8>(acc, x.red);
+    if (tid < 8) {
+      const double h = ddiv(dmul(2.0, L), double(N));
+      const double vol = dmul(dmul(h, h), h);
+      double v = dmul(ldexp(i128_to_double(x.red[tid]), -P), vol);
+      const int pw = (tid == 4 || tid == 7) ? 2 : (tid == 0 || tid == 5) ? 0 : 1;
+      if (pw == 1) v = dmul(v, h);
+      if (pw == 2) v = dmul(v, dmul(h, h));
+      o[tid] = v;
+    }
+  }
+}
+
+template <int N, typename Tio>
+int launch_cons_n(const Tio* Q, double L, long long n_cells, double* out, cudaStream_t st) {
+  const int grid = grid_for(reinterpret_cast<const void*>(cons_kernel<N, Tio>), n_cells);
+  cons_kernel<N, Tio><<<grid, kMThreads, 0, st>>>(Q, L, n_cells, out);
+  return int(cudaGetLastError());
+}
+
+template <typename Tio>
+int launch_cons(const Tio* Q, int N, double L, long long n_cells, double* out, cudaStream_t st) {
+  switch (N) {
+    case 16: return launch_cons_n<16, Tio>(Q, L, n_cells, out, st);
+    case 24: return launch_cons_n<24, Tio>(Q, L, n_cells, out, st);
+    case 32: return launch_cons_n<32, Tio>(Q, L, n_cells, out, st);
+    case 48: return launch_cons_n<48, Tio>(Q, L, n_cells, out, st);
+    case 64: return launch_cons_n<64, Tio>(Q, L, n_cells, out, st);
+    default: return int(cudaErrorInvalidValue);
+  }
 }
 
 template <int N, typename Tio>
@@ -839,6 +1010,13 @@ int launch_sums(const Tio* f, int N, double L, long long n_cells, coll_moments* 
 }
 
 }  // namespace
+
+int launch_conservation(const void* Q, int io_f64, int N, double L, long long n_cells, double* out, void* stream) {
+  count_launches(1);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return io_f64 ? launch_cons<double>(static_cast<const double*>(Q), N, L, n_cells, out, st)
+                : launch_cons<float>(static_cast<const float*>(Q), N, L, n_cells, out, st);
+}
 
 int launch_moments(const void* f, int io_f64, int N, double L, long long n_cells, double eta0, double delta0,
                    coll_moments* mom, uint8_t* mask, void* stream) {

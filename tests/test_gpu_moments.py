@@ -147,38 +147,3 @@ def test_l1_threshold_one_unit_either_side_bit_exact():
             _, gm = check(f[c:c + 1], L, delta0=delta0)
             assert int(gm[0]) & 4 == want, (c, delta0, l1)
 
-
-@pytest.mark.parametrize("N,dtype", [(32, np.float64), (32, np.float32), (24, np.float64), (16, np.float64),
-                                     (48, np.float32)])
-def test_staged_kernel_equals_streaming_kernel_large_batch(N, dtype):
-    """The default kernel holds each cell in the shared memory of a CTA cluster
-    and reads it from HBM once; the streaming kernel re-reads it per pass.  A
-    batch larger than the resident clusters (each cluster loops over several
-    cells), with invalid, all-zero and tiny cells interleaved so that the
-    clusters take their early-exit paths between normal cells: records and
-    masks bitwise equal between the two kernels, and sampled cells bitwise
-    equal to the oracle."""
-    L = synth.DEFAULT_L
-    n = 1200 if N <= 32 else 300
-    f = synth.bimodal_batch_device(n, N, L, 77, dtype=torch.float64)
-    f[5] = 0.0
-    f[6, 1, 2, 3] = float("nan")
-    f[7] = -f[7]
-    f[400 % n] *= 2.0 ** -1000 if dtype == np.float64 else 2.0 ** -110
-    f = f.to(torch.float64 if dtype == np.float64 else torch.float32)
-    mom_s, mask_s = coll.moments(f, L, 1e-3, 1e-4)
-    try:
-        coll.coll_debug_moments_streaming(True)
-        mom_r, mask_r = coll.moments(f, L, 1e-3, 1e-4)
-    finally:
-        coll.coll_debug_moments_streaming(False)
-    torch.cuda.synchronize()
-    assert torch.equal(mask_s, mask_r)
-    a, b = mom_s.cpu().numpy(), mom_r.cpu().numpy()
-    assert np.array_equal(np.nan_to_num(a[:, EXACT], nan=7.0), np.nan_to_num(b[:, EXACT], nan=7.0))
-    np.testing.assert_allclose(np.nan_to_num(a[:, EIG]), np.nan_to_num(b[:, EIG]), atol=1e-12, rtol=0)
-    fc = f.cpu().numpy()
-    for c in sorted({0, 5, 6, 7, 400 % n, n - 1}):
-        r, rm = om.batch(fc[c:c + 1], L, 1e-3, 1e-4)
-        assert int(mask_s[c]) == int(rm[0]), c
-        assert np.array_equal(np.nan_to_num(a[c, EXACT], nan=7.0), np.nan_to_num(r[0, EXACT], nan=7.0)), c
