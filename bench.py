@@ -902,7 +902,7 @@ def run_ours(args, rank, world, local_rank):
     rg_tf = rg["flops"] / (rg["ms"] / 1e3) / 1e12
     line["ragged"] = {
         "kernel": "ragged_kernel<float, float, 16, 24, 32, 48> (persistent, cells taken from a device counter, "
-                  "largest N first), memset + launch captured in a CUDA graph",
+                  "costliest cells first), memset + launch captured in a CUDA graph",
         "workload": "256 x 256 spatial grid, ~15 % Boltzmann mask in curved shock bands, N iid over "
                     "{16, 24, 32, 48}, FP32 anisotropic-temperature cells, hard spheres, M = 48, Mr = 16",
         "cells": rg["cells"], "cells_per_N": rg["cells_per_N"], "ms_per_launch": rg["ms"],

@@ -194,8 +194,9 @@ coll_status coll_eval_batch_static(coll_plan plan, const void* f, void* Q, int64
  * Ragged batch: n_groups (1 .. 256) groups, each with its own plan (its own N,
  * lambda, quadrature), its own f and Q arrays and cells_per_group[g] cells,
  * evaluated in ONE persistent launch: CTAs take cells from a device counter,
- * groups ordered by decreasing N so the largest cells start first.  Every
- * plan must live on the current device and use the same compute type, with
+ * groups ordered by decreasing work per cell (terms x N^3 log N^3) so the
+ * costliest cells start first.  Every plan must live on the current device
+ * and use the same compute type, with
  * the io type that goes with it (COLL_F32: float io; COLL_F64 and COLL_F32X2:
  * double io); otherwise COLL_EUNSUPPORTED.  Results are bitwise identical to
  * coll_eval_batch of each group alone (same per-cell code and order of

@@ -46,8 +46,17 @@ size_t ws_need(const coll_plan_s* p, long long n_cells) {
   return b;
 }
 
+// Work of one cell of a plan, in units of N^3 log2 N^3 (the transforms'
+// count): every term costs one complex inverse 3D transform of N^3 points.
+double cell_cost(const coll_plan_s* p) {
+  const double n3 = double(p->d.N) * p->d.N * p->d.N;
+  return double(p->n_terms) * n3 * std::log2(n3);
+}
+
 // Validate a ragged request and build its launch table: groups sorted by
-// decreasing N (largest cells scheduled first), prefix sums of cell counts.
+// decreasing cost per cell (terms x N^3 log N^3; the costliest cells are
+// scheduled first so that the cheap ones fill the tail), prefix sums of cell
+// counts.
 coll_status ragged_prepare(const coll_cell_group* groups, const int64_t* cells, int32_t n, RaggedTable* t,
                            int* ctype, int* grid, size_t* ws_per_cta, size_t* total_bytes) {
   if (!groups || !cells || n <= 0 || n > kMaxRaggedGroups) return COLL_EINVAL;
@@ -67,8 +76,8 @@ coll_status ragged_prepare(const coll_cell_group* groups, const int64_t* cells, 
     if (cells[i] > 0 && (!groups[i].f || !groups[i].Q || groups[i].f == groups[i].Q)) return COLL_EINVAL;
     order[i] = i;
   }
-  for (int i = 1; i < n; ++i)                       // stable insertion sort, N descending
-    for (int j = i; j > 0 && groups[order[j]].plan->d.N > groups[order[j - 1]].plan->d.N; --j) {
+  for (int i = 1; i < n; ++i)                       // stable insertion sort, cost per cell descending
+    for (int j = i; j > 0 && cell_cost(groups[order[j]].plan) > cell_cost(groups[order[j - 1]].plan); --j) {
       const int tmp = order[j];
       order[j] = order[j - 1];
       order[j - 1] = tmp;

@@ -42,10 +42,13 @@
 // split the tiles of every pass, meet at a cluster barrier between passes and
 // exchange the pass maxima through distributed shared memory, so the cell's
 // float-pair workspace (1 MB at N = 32) is shared by two SMs and the
-// workspaces of all resident cells stay in L2.  Two warpgroups per CTA
-// (shared memory at N = 32: 64 KB per A tile + 56 KB of matrices); each
-// warpgroup owns three accumulators of 2N tensor-memory columns.  Every
-// mbarrier wait is bounded as in mixed.cu.
+// workspaces of all resident cells stay in L2.  Two tile groups per CTA
+// (shared memory at N = 32: 64 KB per A tile + 56 KB of matrices), each of
+// two warpgroups that stage one 128-row tile together (half of its rows each)
+// and drain its three accumulators of 2N tensor-memory columns together (half
+// of the columns each): 16 warps per SM hide the L2 latency of the staging
+// loads and the FP32 chains of slicing and combining.  Every mbarrier wait is
+// bounded as in mixed.cu.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -84,8 +87,9 @@ __host__ __device__ constexpr bool sl_pair_first(int i) { return i == 0 || i == 
 
 template <int N> struct SlCfg {
   static constexpr int H = N / 2;
-  static constexpr int WG = 2;                             // warpgroups per CTA (shared memory bound at N = 32)
-  static constexpr int THREADS = 128 * WG;
+  static constexpr int WG = 2;                             // tile groups per CTA (shared memory bound at N = 32)
+  static constexpr int TGT = 256;                          // threads per tile group: two warpgroups
+  static constexpr int THREADS = TGT * WG;
   static constexpr int KP = 2 * N;                         // f16 values per part per row
   static constexpr int KS = KP / 16;                       // 16-wide K steps per part
   static constexpr int KROW = kSlParts * KP;               // values per A row
@@ -171,6 +175,19 @@ __device__ __forceinline__ void pass_scales(float m, float unit, float* in, floa
 
 enum SlPass : int { kSF2 = 0, kSF1, kSF0, kSX, kSY, kSZ };
 
+// barriers of one tile group (two warpgroups, 256 threads; named barrier tg + 1)
+__device__ __forceinline__ void tg_sync(int tg) { asm volatile("bar.sync %0, 256;" ::"r"(tg + 1) : "memory"); }
+// true iff p holds on all 256 threads of the tile group
+__device__ __forceinline__ bool tg_all(int tg, bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n bar.red.and.pred q, %1, 256, q;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"(tg + 1), "r"(static_cast<uint32_t>(p))
+      : "memory");
+  return r != 0;
+}
+
 struct SlShared {
   uint64_t bar[kSlMaxWG];
   uint64_t tbar[kSlMaxWG];   // teardown: one fresh commit per warpgroup after an expired wait
@@ -214,8 +231,8 @@ struct SlCell {
   // (rows (v0, v1) of f, real values at slots v2) and F1, F0, Y, Z (rows of the
   // pass buffer) take one slot per lane, N sweeps in chunks of 8; pass X takes
   // H lanes per row, H sweeps in chunks of 2 (four loads per sweep).
-  static constexpr int BQ = 4;
-  static constexpr int XQ = 2;
+  static constexpr int BQ = 2;
+  static constexpr int XQ = 1;
   struct PreF { Tio v[BQ]; };
   struct PreBuf { float4 v[BQ]; };
   struct PreX { float4 F[XQ], T[XQ], G[XQ], U[XQ]; };
@@ -291,30 +308,35 @@ struct SlCell {
     }
   }
 
-  // the whole A tile from its first chunk `a` (already loaded); chunk c + 1
-  // loads while chunk c is split (a rolled loop over chunk pairs keeps the code
-  // small); `a` is consumed
+  // Half h of the A tile (chunks h, h + 2, ...; the tile group's other
+  // warpgroup stages the rest) from its first chunk `a` (already loaded); the
+  // next chunk of the half loads while the current one is split (a rolled
+  // loop over chunk pairs keeps the code small); `a` is consumed
   template <int NC, class P>
   static __device__ __forceinline__ void stage(P& a, const Tio* __restrict__ f, const float4* src,
-                                               const float4* __restrict__ tab_t, int ti, int lt,
+                                               const float4* __restrict__ tab_t, int ti, int lt, int h,
                                                unsigned char* atile, float sc) {
-    static_assert(NC % 2 == 0, "chunk pairs");
+    constexpr int NH = NC / 2;
+    static_assert(NC % 2 == 0 && NH % 2 == 0, "chunk pairs per half");
     P b;
 #pragma unroll 1
-    for (int c = 0; c < NC; c += 2) {
-      load(b, f, src, tab_t, ti, lt, c + 1);
-      put_chunk(a, lt, c, atile, sc);
-      if (c + 2 < NC) load(a, f, src, tab_t, ti, lt, c + 2);
-      put_chunk(b, lt, c + 1, atile, sc);
+    for (int i = 0; i < NH; i += 2) {
+      load(b, f, src, tab_t, ti, lt, 2 * (i + 1) + h);
+      put_chunk(a, lt, 2 * i + h, atile, sc);
+      if (i + 2 < NH) load(a, f, src, tab_t, ti, lt, 2 * (i + 2) + h);
+      put_chunk(b, lt, 2 * (i + 1) + h, atile, sc);
     }
   }
 
-  // One pass over this warpgroup's tiles.  Returns false (uniformly over the
-  // warpgroup) if an MMA wait expired; the expired phase stays pending.  `kind`
-  // selects the A-tile source (0: f, pass F2; 1: F and the term table, pass X;
-  // 2: the pass buffer, passes F1, F0, Y, Z, told apart at run time).
+  // One pass over this tile group's tiles.  Returns false (uniformly over the
+  // tile group) if an MMA wait expired; the expired phase stays pending.
+  // `kind` selects the A-tile source (0: f, pass F2; 1: F and the term table,
+  // pass X; 2: the pass buffer, passes F1, F0, Y, Z, told apart at run time).
+  // tg: tile group; lt2: thread of the tile group (0 .. 255), whose warpgroup
+  // half h = lt2 / 128 stages half of each tile and drains half of its output
+  // columns.
   template <int kind>
-  static __device__ __forceinline__ bool run(int pass, int wg, int lt, unsigned char* atile, uint32_t abase,
+  static __device__ __forceinline__ bool run(int pass, int wg, int lt2, unsigned char* atile, uint32_t abase,
                                              uint32_t bbase, uint32_t tacc, uint32_t& phase, bool& pending,
                                              SlShared& sh, const Tio* __restrict__ f, Tio* __restrict__ Q,
                                              float4* Fs, float4* buf, float2* G, const float4* __restrict__ tab_t,
@@ -326,7 +348,13 @@ struct SlCell {
     // F0 writes F and Z accumulates G in true units (times sc_out); the other
     // passes store their outputs in level-0 units of the pass
     const bool to_true = kind == 2 && (pass == kSF0 || pass == kSZ);
-    const int q = lt >> 5;
+    const int h = lt2 >> 7, lt = lt2 & 127;
+    const int q = lt >> 5;                               // TMEM lane quarter of this warp
+    // output columns drained by this half, in chunks of CW columns (CW / 2
+    // complex outputs)
+    constexpr int CW = 8, EW = CW / 2;
+    constexpr int CPH = nout / 2;
+    const int c_begin = h * CPH, c_end = (h + 1) * CPH < nout ? (h + 1) * CPH : nout;
     float lmax = 0.0f;
     using Pre = typename std::conditional<kind == 0, PreF,
                                           typename std::conditional<kind == 1, PreX, PreBuf>::type>::type;
@@ -335,15 +363,15 @@ struct SlCell {
     const float4* src = kind == 1 ? Fs : buf;
     Pre pre;
     const int ti0 = crank * kWG + wg;
-    if (ti0 < rows / 128) load(pre, f, src, tab_t, ti0, lt, 0);
+    if (ti0 < rows / 128) load(pre, f, src, tab_t, ti0, lt, h);
     for (int ti = ti0; ti < rows / 128; ti += 2 * kWG) {
       const int r = ti * 128 + lt;
       // ---- A tile
-      stage<NC>(pre, f, src, tab_t, ti, lt, atile, sc_in);
+      stage<NC>(pre, f, src, tab_t, ti, lt, h, atile, sc_in);
       fence_async_smem();
-      wg_sync(wg);
+      tg_sync(wg);
       // ---- MMAs: ten products into three accumulators
-      if (lt == 0) {
+      if (lt2 == 0) {
         fence_after();
         const uint32_t id = idesc_f16(128, nout, 0);
         // descriptors of the tile bases; each K step adds a compile-time offset
@@ -365,9 +393,9 @@ struct SlCell {
         mma_commit(&sh.bar[wg]);
       }
       // the next tile's first chunk is in flight during the MMAs and the epilogue
-      if (ti + 2 * kWG < rows / 128) load(pre, f, src, tab_t, ti + 2 * kWG, lt, 0);
-      if (!wg_all(wg, wait_parity(&sh.bar[wg], phase))) {
-        if (lt == 0) {
+      if (ti + 2 * kWG < rows / 128) load(pre, f, src, tab_t, ti + 2 * kWG, lt, h);
+      if (!tg_all(wg, wait_parity(&sh.bar[wg], phase))) {
+        if (lt2 == 0) {
           st_cluster_u32(cluster_addr(su32(&sh.abort), 0), 1u);
           st_cluster_u32(cluster_addr(su32(&sh.abort), 1), 1u);
         }
@@ -378,29 +406,27 @@ struct SlCell {
       fence_after();
       // ---- epilogue: thread = TMEM lane = pencil row r
       const uint32_t lane_base = static_cast<uint32_t>(32 * q) << 16;
-      // pass Z: the gain accumulator of the chunk's 8 outputs, loaded one chunk ahead
-      float2 gcur[8], gnxt[8];
+      // pass Z: the gain accumulator of the chunk's outputs, loaded one chunk ahead
+      float2 gcur[EW], gnxt[EW];
       const bool zacc = kind == 2 && pass == kSZ && !first_term;
       if (zacc) {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) gcur[e] = __ldcg(G + size_t(e) * N * N + r);
+        for (int e = 0; e < EW; ++e) gcur[e] = __ldcg(G + size_t(c_begin / 2 + e) * N * N + r);
       }
 #pragma unroll 1
-      for (int c0 = 0; c0 < nout; c0 += 16) {
-        if (zacc && c0 + 16 < nout) {
+      for (int c0 = c_begin; c0 < c_end; c0 += CW) {
+        if (zacc && c0 + CW < c_end) {
 #pragma unroll
-          for (int e = 0; e < 8; ++e) gnxt[e] = __ldcg(G + size_t((c0 + 16) / 2 + e) * N * N + r);
+          for (int e = 0; e < EW; ++e) gnxt[e] = __ldcg(G + size_t((c0 + CW) / 2 + e) * N * N + r);
         }
-        uint32_t u0[16], u1[16], u2[16];
-        tld16_nw(tacc + lane_base + c0, u0);
-        tld16_nw(tacc + C::NOUT + lane_base + c0, u1);
-        tld16_nw(tacc + 2 * C::NOUT + lane_base + c0, u2);
-        tld_wait(u0);
-        tld_tie(u1);
-        tld_tie(u2);
+        uint32_t u0[CW], u1[CW], u2[CW];
+        tld8_nw(tacc + lane_base + c0, u0);
+        tld8_nw(tacc + C::NOUT + lane_base + c0, u1);
+        tld8_nw(tacc + 2 * C::NOUT + lane_base + c0, u2);
+        tld8_wait(u0, u1, u2);
         const int v0c = c0 >> 1;                         // first complex output of this chunk
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
+        for (int e = 0; e < EW; ++e) {
           df re = combine(u0[2 * e], u1[2 * e], u2[2 * e]);
           df im = combine(u0[2 * e + 1], u1[2 * e + 1], u2[2 * e + 1]);
           if (to_true) {                                // passes F0 and Z: true units
@@ -445,11 +471,11 @@ struct SlCell {
         }
         if (zacc) {
 #pragma unroll
-          for (int e = 0; e < 8; ++e) gcur[e] = gnxt[e];
+          for (int e = 0; e < EW; ++e) gcur[e] = gnxt[e];
         }
       }
       fence_before();
-      wg_sync(wg);
+      tg_sync(wg);
     }
     if (next_slot >= 0) {
       // warp maximum, then into the slot of both CTAs of the cluster
@@ -467,7 +493,7 @@ struct SlCell {
                               const float* __restrict__ tmax, int n_terms, unsigned char* ws, unsigned char* atile,
                               uint32_t abase, uint32_t bbase, uint32_t tacc, uint32_t& phase, bool& pending,
                               SlShared& sh, bool& bad) {
-    const int tid = threadIdx.x, wg = tid >> 7, lt = tid & 127;
+    const int tid = threadIdx.x, wg = tid >> 8, lt = tid & 255;   // tile group, its thread
     float4* Fs = reinterpret_cast<float4*>(ws);
     float4* buf = reinterpret_cast<float4*>(ws + C::F_BYTES);
     float2* G = reinterpret_cast<float2*>(ws + C::F_BYTES + C::BUF_BYTES);
@@ -531,7 +557,7 @@ __global__ void __launch_bounds__(SlCfg<N>::THREADS, 1) sliced_kernel(CollArgs a
   using C = SlCfg<N>;
   extern __shared__ __align__(1024) unsigned char smraw[];
   __shared__ SlShared sh;
-  const int tid = threadIdx.x, warp = tid >> 5, wg = tid >> 7;
+  const int tid = threadIdx.x, warp = tid >> 5, wg = tid >> 8;   // wg: tile group (two warpgroups)
   const uint32_t raw = su32(smraw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* sm = smraw + (base - raw);
@@ -576,12 +602,12 @@ __global__ void __launch_bounds__(SlCfg<N>::THREADS, 1) sliced_kernel(CollArgs a
                              phase, pending, sh, bad))
       break;
   }
-  // A wait that expired may leave this warpgroup's last MMA batch in flight.
+  // A wait that expired may leave this tile group's last MMA batch in flight.
   // A fresh commit from the issuing thread to a barrier of its own arrives once
   // every MMA that thread started has completed; tensor memory is freed only
   // after that arrival (bounded wait).
   if (pending) {
-    if ((tid & 127) == 0) mma_commit(&sh.tbar[wg]);
+    if ((tid & 255) == 0) mma_commit(&sh.tbar[wg]);
     (void)wait_parity(&sh.tbar[wg], 0);
   }
   fence_before();

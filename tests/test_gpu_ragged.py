@@ -163,3 +163,32 @@ def test_config4_full_workload_graph():
             assert np.linalg.norm(got - want) / np.linalg.norm(want) <= TOL["f32"], (N, c)
     for p in plans:
         p.close()
+
+
+def test_ragged_mixed_lambda_cost_order():
+    """Maxwell-molecule groups (lambda = 0: Mr times the terms of a hard-sphere
+    cell) beside hard-sphere groups in one launch: the costliest groups are
+    scheduled first whatever their N, and every group still equals its own
+    launch bitwise and the oracle on a sampled cell."""
+    specs = [(32, 1.0, 16, 3), (16, 0.0, 8, 5), (24, 1.0, 16, 4), (24, 0.0, 8, 2)]
+    r = synth.rng(17)
+    plans, fs, Qs, counts = [], [], [], []
+    for N, lam, Mr, n in specs:
+        plans.append(coll.Plan(N, L, lam=lam, M=32, Mtheta=4, Mr=Mr, prec="f32", max_cells=n))
+        cells = np.stack([synth.anisotropic_cell(N, L, r, dtype=np.float64) for _ in range(n)])
+        fs.append(torch.from_numpy(cells).to("cuda", torch.float32))
+        Qs.append(torch.full_like(fs[-1], float("nan")))
+        counts.append(n)
+    groups = [(p.handle, f, Q) for p, f, Q in zip(plans, fs, Qs)]
+    ws = torch.empty(coll.coll_ragged_workspace_size(groups, counts), dtype=torch.uint8, device="cuda")
+    coll.coll_eval_ragged(groups, counts, ws)
+    torch.cuda.synchronize()
+    for (N, lam, Mr, n), p, f, Q in zip(specs, plans, fs, Qs):
+        assert p.status() == coll.COLL_OK
+        assert torch.equal(Q, p.eval(f)), (N, lam)
+        pr = Params(N=N, L=L, lam=lam, M=32, Mtheta=4, Mr=Mr)
+        want = q_fast(f[0].double().cpu().numpy(), pr)
+        got = Q[0].double().cpu().numpy()
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) <= TOL["f32"], (N, lam)
+    for p in plans:
+        p.close()
