@@ -911,7 +911,7 @@ def run_ours(args, rank, world, local_rank):
                      "peak_basis": "FP32 pipe (as the 2D FP32 line)", "flops_per_launch": rg["flops"]}}
     if args.serve_requests > 0:
         from paper_2505_03360_gb300.service import Service, stream_jobs
-        svc = Service(hbm_budget_bytes=120e9, device=str(dev))
+        svc = Service(hbm_budget_bytes=120e9, device=str(dev), max_wall_s=args.serve_max_wall)
         svc.warm_plans()
         jobs = stream_jobs(n_requests=args.serve_requests, rate_per_s=200.0, max_cells=args.serve_max_cells)
         _, st = svc.run(jobs, realtime=True)
@@ -922,7 +922,12 @@ def run_ours(args, rank, world, local_rank):
                         "(f += 1e-2 Q between), HBM budget 120 GB" % (args.serve_requests, args.serve_max_cells + 1),
             "cell_evals_per_s": st["cell_evals_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "requests": st["requests"], "wall_s": st["wall_s"], "peak_hbm_gb": st["peak_hbm_bytes"] / 1e9,
-            "max_queue_depth": st["max_queue_depth"], "ragged_launches": st["ragged_launches"]}
+            "max_queue_depth": st["max_queue_depth"], "ragged_launches": st["ragged_launches"],
+            "requests_by_compute_type": st["requests_by_compute_type"],
+            "conservation_rel_max": st["conservation_rel_max"],
+            "mass_rel_max_by_compute_type": st["mass_rel_max_by_compute_type"],
+            "precision_classes": "f32: FP32 kernels; mixed: fixed-point-slice tensor cores (<= 1e-6 vs FP64) at "
+                                 "N = 16, 32, FP32 kernels at N = 48, 64"}
     if not args.no_cpu_baseline:
         ncell = 48
         tcpu = oracle_sample(ncell)
@@ -952,7 +957,10 @@ def main():
                     help="time the main path only (no e2e, no variants): for short profiler captures")
     ap.add_argument("--serve-requests", type=int, default=100,
                     help="requests of the serving stream measured beside the main line (0: skip)")
-    ap.add_argument("--serve-max-cells", type=int, default=64)
+    ap.add_argument("--serve-max-cells", type=int, default=64,
+                    help="largest request (cells); the full serving workload is --serve-requests 2000 "
+                         "--serve-max-cells 2048 (several minutes)")
+    ap.add_argument("--serve-max-wall", type=float, default=1800.0)
     ap.add_argument("--profile-m2d", default=None, choices=["f64", "f32x2", "f32"],
                     help="run only the 2D Maxwell operator (two launches) for profiler captures")
     ap.add_argument("--m2d-cells", type=int, default=M2D_WORKLOAD["cells"])

@@ -2,8 +2,8 @@
 
 Requests (cells x N^3, lambda, precision, a number of repeated evaluations)
 arrive over time.  Between GPU iterations the loop admits waiting requests in
-arrival order while they fit the HBM budget (f, Q and a share of the ragged
-workspace) and keeps every admitted request's f resident on the device.  Each
+arrival order while they fit the HBM budget (f, Q and the workspace of the
+request's cells) and keeps every admitted request's f resident on the device.  Each
 iteration evaluates the active requests oldest first, up to a cost budget per
 iteration (at least one request), so that early requests finish early instead
 of every request advancing in lockstep: ONE ragged persistent launch per SIMT
@@ -15,10 +15,13 @@ Latency is measured from arrival to the completion of the request's last
 evaluation.
 
 Precision classes: "f32" runs the FP32 kernels; "mixed" runs the tensor-core
-DFT-GEMM path (f16 hi+lo, COLL_MIXED_F16X2) where it supports the grid
-(N = 16, 32) and FP32 above.  Each cell's arithmetic does not depend on what
-else is in the batch, so a request's result is the same alone and in the mix
-(tests/test_gpu_service.py).
+fixed-point-slice path (COLL_MIXED_SLICED, within 1e-6 of FP64 per cell) where
+it supports the grid (N = 16, 32) and the FP32 kernels above (N = 48, 64 have no
+tensor-core path); every finished request records the compute type it ran in
+and the conservation errors of its last Q (coll_conservation: mass, momentum
+and energy relative to the |Q|-weighted integrals), so no result leaves without
+a stated accuracy.  Each cell's arithmetic does not depend on what else is in
+the batch, so a request's result is the same alone and in the mix.
 """
 from __future__ import annotations
 
@@ -39,14 +42,18 @@ def torch_event(stream):
     e.record(stream)
     return e
 
+TENSOR = ("mixed_sliced", "mixed_f16x2", "mixed_bf16x3")     # compute types without ragged launches
+
+
 def effective_precision(precision: str, N: int) -> str:
+    """The compute type a request of class `precision` runs in at grid size N."""
     if precision == "mixed":
-        return "mixed_f16x2" if N in (16, 32) else "f32"
+        return "mixed_sliced" if N in (16, 32) else "f32"
     return precision
 
 
 # relative GPU time per cell-evaluation by compute type (measured at N = 32, 25 terms)
-SPEED = {"f32": 1.0, "mixed_f16x2": 0.83, "f32x2": 7.6, "f64": 23.0}
+SPEED = {"f32": 1.0, "mixed_sliced": 3.2, "mixed_f16x2": 0.83, "f32x2": 7.6, "f64": 23.0}
 
 
 def cell_cost(N: int, lam: float, prec: str, M: int = 48, Mr: int = 8) -> float:
@@ -74,11 +81,13 @@ class Job:
     bytes: int = 0
     t_admit: float = None
     t_finish: float = None
+    compute: str = None             # the compute type the request ran in
+    cons_err: tuple = None          # relative (mass, momentum, energy) errors of the last Q, worst cell
 
 
 class Service:
     def __init__(self, hbm_budget_bytes: float = 120e9, L: float = synth.DEFAULT_L, M: int = 48, Mtheta: int = 4,
-                 device: str = "cuda", iter_budget_cells: float = 2048.0):
+                 device: str = "cuda", iter_budget_cells: float = 2048.0, max_wall_s: float = 600.0):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -96,13 +105,14 @@ class Service:
         # cost budget of one iteration, in N = 32, lambda = 1, FP32 cell-evaluations
         self.iter_budget = iter_budget_cells * cell_cost(32, 1.0, "f32", M=M)
         self.min_cells = 2 * torch.cuda.get_device_properties(self.device).multi_processor_count
+        self.max_wall_s = max_wall_s
 
     # ---------------------------------------------------------------- plans
     def plan(self, N: int, lam: float, prec: str):
         key = (N, float(lam), prec)
         if key not in self.plans:
             Mr = 16 if lam == 1.0 else 8
-            io = 1 if prec in ("f32", "mixed_f16x2") else 0
+            io = 1 if prec in ("f32",) + TENSOR else 0
             self.plans[key] = coll.Plan(N, self.L, lam=lam, M=self.M, Mtheta=self.Mtheta, Mr=Mr, prec=prec,
                                         io_dtype=io, max_cells=1, device=self.device)
         return self.plans[key]
@@ -111,7 +121,7 @@ class Service:
         """Tensor-core plan for job j and the workspace of side stream `lane`: one
         plan per (N, lambda) serves every lane (a plan is immutable; each
         concurrent launch needs only its own workspace)."""
-        p = self.plan(j.N, j.lam, "mixed_f16x2")
+        p = self.plan(j.N, j.lam, effective_precision(j.precision, j.N))
         need = max(256, coll.coll_workspace_size(p.handle, max(1, j.n_cells)))
         ws = self.lane_ws.get(lane)
         if ws is None or ws.numel() < need:
@@ -134,7 +144,7 @@ class Service:
                     dt = torch.float64 if prec in ("f32x2", "f64") else torch.float32
                     f = torch.zeros((1, N, N, N), dtype=dt, device=self.device)
                     Q = torch.empty_like(f)
-                    if prec == "mixed_f16x2":
+                    if prec in TENSOR:
                         for lane in range(len(self.side)):
                             j = Job(rid=-1, arrival_s=0.0, n_cells=1, N=N, lam=lam, precision=p)
                             pl, ws = self._mix_plan(j, lane)
@@ -151,9 +161,12 @@ class Service:
 
     # -------------------------------------------------------------- memory
     def _job_bytes(self, j: Job) -> int:
+        """f and Q of the request plus the workspace its cells need (an upper
+        bound: the ragged launch shares one workspace between requests)."""
         prec = effective_precision(j.precision, j.N)
         es = 8 if prec in ("f32x2", "f64") else 4
-        return 2 * j.n_cells * j.N ** 3 * es
+        ws = coll.coll_workspace_size(self.plan(j.N, j.lam, prec).handle, max(1, j.n_cells))
+        return 2 * j.n_cells * j.N ** 3 * es + ws
 
     def _ensure_ws(self, nbytes: int):
         if self.ws is None or self.ws.numel() < nbytes:
@@ -199,7 +212,7 @@ class Service:
             by_kind[effective_precision(j.precision, j.N)].append(j)
         side_used = []
         for prec, jobs in by_kind.items():
-            if prec == "mixed_f16x2":
+            if prec in TENSOR:
                 ready = torch_event(self.stream)
                 for i, j in enumerate(jobs):
                     st = self.side[i % len(self.side)]
@@ -222,17 +235,25 @@ class Service:
         for j in chosen:
             if j.done + 1 < j.n_evals:
                 coll.coll_advance(j.f, j.Q, j.dt, stream=self.stream)
+        # requests whose last evaluation this was: conservation check of the last Q
+        last = [j for j in chosen if j.done + 1 >= j.n_evals]
+        invs = [coll.conservation(j.Q, self.L, stream=self.stream) for j in last]
         self.stream.synchronize()
         for j in chosen:
             j.done += 1
             self.stats["cell_evals"] += j.n_cells
+        for j, inv in zip(last, invs):
+            e = self.torch.nan_to_num(coll.conservation_errors(inv), nan=0.0).amax(0)
+            j.cons_err = tuple(float(x) for x in e.cpu())
+            j.compute = effective_precision(j.precision, j.N)
 
     # ----------------------------------------------------------------- run
-    def run(self, jobs, realtime: bool = True, max_wall_s: float = 600.0, keep_outputs: bool = False):
+    def run(self, jobs, realtime: bool = True, max_wall_s: float = None, keep_outputs: bool = False):
         """Serve jobs (sorted by arrival).  Returns finished jobs and a stats dict.
         realtime=False advances a simulated clock by the measured GPU time
         (deterministic admission order); keep_outputs keeps each finished
         job's final f and last Q on the device."""
+        max_wall_s = self.max_wall_s if max_wall_s is None else max_wall_s
         pending = collections.deque(sorted(jobs, key=lambda j: j.arrival_s))
         waiting = collections.deque()
         active, finished = [], []
@@ -281,6 +302,10 @@ class Service:
             active = still
         wall = time.perf_counter() - t0 if realtime else clock
         lat = np.array([j.t_finish - j.arrival_s for j in finished])
+        cons = np.array([j.cons_err for j in finished if j.cons_err is not None]).reshape(-1, 3)
+        by_type = collections.defaultdict(list)
+        for j in finished:
+            by_type[j.compute].append(j.cons_err[0] if j.cons_err else float("nan"))
         stats = {
             "requests": len(finished),
             "cell_evals": int(self.stats["cell_evals"]),
@@ -292,6 +317,10 @@ class Service:
             "hbm_budget_bytes": self.budget,
             "max_queue_depth": int(max_q),
             "ragged_launches": int(self.stats["launches"]),
+            "requests_by_compute_type": {k: len(v) for k, v in sorted(by_type.items())},
+            "conservation_rel_max": ({"mass": float(cons[:, 0].max()), "momentum": float(cons[:, 1].max()),
+                                      "energy": float(cons[:, 2].max())} if cons.size else None),
+            "mass_rel_max_by_compute_type": {k: float(np.nanmax(v)) for k, v in sorted(by_type.items())},
         }
         return finished, stats
 

@@ -57,19 +57,42 @@ def test_alone_equals_in_mix():
     svc2.close()
 
 
-@pytest.mark.parametrize("precision,lam", [("f32", 1.0), ("mixed", 0.0)])
-def test_single_evaluation_matches_oracle(precision, lam):
-    N = 16
+@pytest.mark.parametrize("precision,lam,N", [("f32", 1.0, 16), ("mixed", 0.0, 16), ("mixed", 0.0, 32),
+                                             ("f32", 0.0, 32)])
+def test_single_evaluation_matches_oracle(precision, lam, N):
+    """One evaluation through the service against the oracle, Maxwell molecules
+    included at N = 32: "mixed" runs the fixed-point-slice tensor-core path
+    (1e-6 per cell), "f32" the FP32 kernels (5e-4)."""
     f = synth.bimodal_batch(2, N, synth.DEFAULT_L, seed=61)
     job = Job(0, 0.0, 2, N, lam, precision, n_evals=1, f_host=f)
     svc = Service(hbm_budget_bytes=1e9)
     svc.run([job], realtime=False, keep_outputs=True)
+    assert job.compute == ("mixed_sliced" if precision == "mixed" else "f32")
     Mr = 16 if lam == 1.0 else 8
     p = Params(N=N, L=synth.DEFAULT_L, lam=lam, M=48, Mtheta=4, Mr=Mr)
-    tol = 5e-4 if precision == "f32" else 1e-3      # "mixed" at N = 16: the tensor-core f16 hi+lo path
+    tol = 5e-4 if precision == "f32" else 1e-6
     for c in range(2):
         fin = job.f[c].double().cpu().numpy()
         ref = q_fast(fin, p)
         got = job.Q[c].double().cpu().numpy()
         assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= tol
+    svc.close()
+
+
+def test_every_request_states_compute_type_and_conservation():
+    """Finished requests carry the compute type they ran in and the relative
+    conservation errors of their last Q; mass is conserved to the rounding of
+    that compute type (N = 48, 64 "mixed" requests run the FP32 kernels)."""
+    jobs = stream_jobs(n_requests=16, rate_per_s=1e6, max_cells=4, Ns=(16, 32, 48), n_evals=2)
+    svc = Service(hbm_budget_bytes=1e9)
+    done, st = svc.run(jobs, realtime=False)
+    assert len(done) == 16
+    for j in done:
+        want = ("mixed_sliced" if j.N in (16, 32) else "f32") if j.precision == "mixed" else j.precision
+        assert j.compute == want
+        mass, mom, energy = j.cons_err
+        assert mass <= (1e-5 if j.compute == "mixed_sliced" else 5e-3), (j.compute, j.cons_err)
+        assert np.isfinite(mom) and np.isfinite(energy)
+    assert sum(st["requests_by_compute_type"].values()) == 16
+    assert st["conservation_rel_max"]["mass"] < 5e-3
     svc.close()
