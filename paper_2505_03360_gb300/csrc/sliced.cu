@@ -23,10 +23,13 @@
 // and the like), so the FP32 accumulators of L0 and of 2^-9 L1 (taken against
 // the matrices 2^-9 d1 and 2^-9 d0: multiples of 2^-9 below 2^15) are exact;
 // only L2 rounds, at about 2^-42 of L0's scale.  The products left out are
-// below 2^-45 of it.  Each level has its own tensor-memory accumulator; the
-// epilogue combines them into a normalised float pair (hi + lo, about 48 bits)
-// in units of the level-0 accumulator, and the next pass rescales by a power
-// of two.
+// below 2^-45 of it.  Each level has its own tensor-memory accumulator (L2 two:
+// L2 and L2'); the epilogue combines them into a normalised float pair (hi +
+// lo, about 48 bits) in units of the level-0 accumulator, and the next pass
+// rescales by a power of two.  The matrices are laid out side by side along
+// the MMA's N dimension so that each part of the A tile is read once per K
+// step: s0 [d0 | 2^-9 d1 | d2 | dT] -> (L0, L1, L2, L2'), s1 [2^-9 d0 | d1 |
+// 2^-9 d2] -> (L1, L2, L2'), s2 [d0 | 2^-9 d1] -> (L2, L2'), sT [d0] -> L2'.
 //
 // Intermediates: the forward spectrum F, the pass buffer and the gain
 // accumulator G are float pairs in the CTA's workspace (L2 resident), and the
@@ -37,7 +40,9 @@
 //
 // Layouts and row orders are those of mixed.cu.  A row of the A tile holds the
 // four parts one after another (K index 2N part + 2k + ri); the matrix image
-// holds d0, d1, d2, dT, 2^-9 d1, 2^-9 d2, 2^-9 d0 one after another along K.
+// holds NOUT rows per matrix in the order d0, 2^-9 d1, d2, dT, 2^-9 d0, d1,
+// 2^-9 d2 (each row the 2N K values of one output component, 128-byte
+// swizzled, zero padded to 64 K values).
 // One cluster of two CTAs (two SMs) per cell, persistent over cells: the CTAs
 // split the tiles of every pass, meet at a cluster barrier between passes and
 // exchange the pass maxima through distributed shared memory, so the cell's
@@ -45,7 +50,7 @@
 // workspaces of all resident cells stay in L2.  Two tile groups per CTA
 // (shared memory at N = 32: 64 KB per A tile + 56 KB of matrices), each of
 // two warpgroups that stage one 128-row tile together (half of its rows each)
-// and drain its three accumulators of 2N tensor-memory columns together (half
+// and drain its four accumulators of 2N tensor-memory columns together (half
 // of the columns each): 16 warps per SM hide the L2 latency of the staging
 // loads and the FP32 chains of slicing and combining.  Every mbarrier wait is
 // bounded as in mixed.cu.
@@ -82,6 +87,15 @@ __host__ __device__ constexpr int sl_pair_b(int i) {
   return v[i];
 }
 __host__ __device__ constexpr int sl_pair_acc(int i) { return i == 0 ? 0 : (i < 3 ? 1 : 2); }
+// Row of matrix s in the image (NOUT rows per matrix), grouped so that one MMA
+// of N = 4 NOUT applies [d0 | 2^-9 d1 | d2 | dT] to s0 (accumulators L0, L1,
+// L2, L2'), one of N = 3 NOUT applies [2^-9 d0 | d1 | 2^-9 d2] to s1 (L1, L2,
+// L2'), and prefixes of the first group serve s2 ([d0 | 2^-9 d1]: L2, L2')
+// and sT ([d0]: L2').
+__host__ __device__ constexpr int sl_mat_row(int s, int nout) {
+  constexpr int v[kSlMats] = {0, 5, 2, 3, 1, 6, 4};
+  return v[s] * nout;
+}
 // the first product of each accumulator overwrites it
 __host__ __device__ constexpr bool sl_pair_first(int i) { return i == 0 || i == 1 || i == 3; }
 
@@ -96,10 +110,9 @@ template <int N> struct SlCfg {
   static constexpr int KB = KROW / 64;                     // 128-byte K blocks per A row
   static constexpr int PART_B = 2 * KP;                    // bytes per part in an A row
   static constexpr int NOUT = 2 * N;                       // matrix rows (v, re/im)
-  static constexpr int BK = (kSlMats * KP + 63) / 64 * 64;  // K values of the matrix image (zero padded)
-  static constexpr int B_BYTES = (BK / 64) * NOUT * 128;
+  static constexpr int B_BYTES = kSlMats * NOUT * 128;      // seven matrices of NOUT rows x 64 K values
   static constexpr int A_TILE = KB * 128 * 128;
-  static constexpr int TCOLS_USED = WG * 3 * NOUT;
+  static constexpr int TCOLS_USED = WG * 4 * NOUT;           // accumulators L0, L1, L2, L2' per tile group
   static constexpr int TCOLS = 512;
   static constexpr int SMEM_USED = B_BYTES + WG * A_TILE + 1024;
   // at least half an SM's shared memory, so that no two CTAs (each holding all
@@ -158,9 +171,10 @@ __device__ __forceinline__ df fma2(df a, df b, df c, df d) {
 // below an ulp of the head; without it the tail of a small output would carry
 // the previous pass's scale, and the next slicing's third part would grow
 // from pass to pass past f16's exact integers.
-__device__ __forceinline__ df combine(uint32_t u0, uint32_t u1, uint32_t u2) {
+__device__ __forceinline__ df combine(uint32_t u0, uint32_t u1, uint32_t u2, uint32_t u3) {
   const df s = two_sum(__uint_as_float(u0), __uint_as_float(u1));
-  return quick_two_sum(s.h, __fmaf_rn(__uint_as_float(u2), 0x1p-18f, s.l));
+  const float l2 = __fadd_rn(__uint_as_float(u2), __uint_as_float(u3));   // the two third-level accumulators
+  return quick_two_sum(s.h, __fmaf_rn(l2, 0x1p-18f, s.l));
 }
 
 // Scales of a pass from the maximum modulus m of its input (in the unit of the
@@ -370,24 +384,42 @@ struct SlCell {
       stage<NC>(pre, f, src, tab_t, ti, lt, h, atile, sc_in);
       fence_async_smem();
       tg_sync(wg);
-      // ---- MMAs: ten products into three accumulators
+      // ---- MMAs: ten products into four accumulators (L0, L1 and two for L2)
       if (lt2 == 0) {
         fence_after();
-        const uint32_t id = idesc_f16(128, nout, 0);
         // descriptors of the tile bases; each K step adds a compile-time offset
         // to the 14-bit start-address field (addresses stay below 2^18 bytes,
         // so the field never carries)
         const uint64_t ad = sw128_desc(abase), bd = sw128_desc(bbase);
+        if constexpr (kind == 0) {
+          // real input, N outputs: the ten products one by one into L0, L1, L2
+          const uint32_t id = idesc_f16(128, nout, 0);
 #pragma unroll
-        for (int pi = 0; pi < kSlPairs; ++pi) {
-          const int pa = sl_pair_a(pi), pb = sl_pair_b(pi), pc = sl_pair_acc(pi);
-          const bool first = sl_pair_first(pi);
+          for (int pi = 0; pi < kSlPairs; ++pi) {
+            const int pa = sl_pair_a(pi), pb = sl_pair_b(pi), pc = sl_pair_acc(pi);
+            const bool first = sl_pair_first(pi);
 #pragma unroll
-          for (int j = 0; j < C::KS; ++j) {
-            const int ka = pa * C::KS + j, kb = pb * C::KS + j;
-            mma_f16(tacc + pc * C::NOUT, ad + uint64_t(((ka >> 2) * 16384 + (ka & 3) * 32) >> 4),
-                    bd + uint64_t(((kb >> 2) * (C::NOUT * 128) + (kb & 3) * 32) >> 4), id,
-                    (first && j == 0) ? 0u : 1u);
+            for (int j = 0; j < C::KS; ++j) {
+              const int ka = pa * C::KS + j;
+              mma_f16(tacc + pc * C::NOUT, ad + uint64_t(((ka >> 2) * 16384 + (ka & 3) * 32) >> 4),
+                      bd + uint64_t((sl_mat_row(pb, C::NOUT) * 128 + j * 32) >> 4), id,
+                      (first && j == 0) ? 0u : 1u);
+            }
+          }
+        } else {
+          // one MMA per part and K step over its matrices side by side along N
+#pragma unroll
+          for (int pa = 0; pa < kSlParts; ++pa) {
+            const int brow = pa == 1 ? 4 * C::NOUT : 0;
+            const int ncol = (pa == 0 ? 4 : pa == 1 ? 3 : pa == 2 ? 2 : 1) * C::NOUT;
+            const int dcol = (pa == 0 ? 0 : pa == 1 ? 1 : pa == 2 ? 2 : 3) * C::NOUT;
+            const uint32_t id = idesc_f16(128, ncol, 0);
+#pragma unroll
+            for (int j = 0; j < C::KS; ++j) {
+              const int ka = pa * C::KS + j;
+              mma_f16(tacc + dcol, ad + uint64_t(((ka >> 2) * 16384 + (ka & 3) * 32) >> 4),
+                      bd + uint64_t((brow * 128 + j * 32) >> 4), id, (pa == 0 && j == 0) ? 0u : 1u);
+            }
           }
         }
         mma_commit(&sh.bar[wg]);
@@ -419,16 +451,22 @@ struct SlCell {
 #pragma unroll
           for (int e = 0; e < EW; ++e) gnxt[e] = __ldcg(G + size_t((c0 + CW) / 2 + e) * N * N + r);
         }
-        uint32_t u0[CW], u1[CW], u2[CW];
+        uint32_t u0[CW], u1[CW], u2[CW], u3[CW];
         tld8_nw(tacc + lane_base + c0, u0);
         tld8_nw(tacc + C::NOUT + lane_base + c0, u1);
         tld8_nw(tacc + 2 * C::NOUT + lane_base + c0, u2);
+        if constexpr (kind != 0) tld8_nw(tacc + 3 * C::NOUT + lane_base + c0, u3);
         tld8_wait(u0, u1, u2);
+        if constexpr (kind != 0) tld8_tie(u3);
+        else {
+#pragma unroll
+          for (int e = 0; e < CW; ++e) u3[e] = 0u;             // +0.0f: no second third-level accumulator
+        }
         const int v0c = c0 >> 1;                         // first complex output of this chunk
 #pragma unroll
         for (int e = 0; e < EW; ++e) {
-          df re = combine(u0[2 * e], u1[2 * e], u2[2 * e]);
-          df im = combine(u0[2 * e + 1], u1[2 * e + 1], u2[2 * e + 1]);
+          df re = combine(u0[2 * e], u1[2 * e], u2[2 * e], u3[2 * e]);
+          df im = combine(u0[2 * e + 1], u1[2 * e + 1], u2[2 * e + 1], u3[2 * e + 1]);
           if (to_true) {                                // passes F0 and Z: true units
             re = df{__fmul_rn(re.h, sc_out), __fmul_rn(re.l, sc_out)};
             im = df{__fmul_rn(im.h, sc_out), __fmul_rn(im.l, sc_out)};
@@ -587,7 +625,7 @@ __global__ void __launch_bounds__(SlCfg<N>::THREADS, 1) sliced_kernel(CollArgs a
   fence_after();
   cluster_sync();                          // the peer CTA is running before any remote shared-memory access
   const uint32_t tbase = sh.tbase;
-  const uint32_t tacc = tbase + wg * 3 * C::NOUT;
+  const uint32_t tacc = tbase + wg * 4 * C::NOUT;
   uint32_t phase = 0;
   bool pending = false, bad = false;
   const auto* tab = static_cast<const float4*>(a.tab);
@@ -707,13 +745,14 @@ int sliced_max_ctas_per_sm(int N, bool io_f64, int* ctas) {
 // Device image of a sliced plan: per-term tables [t][k0][k1][k2h] (A_h, A_l,
 // B_h, B_l) as float pairs, the per-term bound max|A + iB| (rounded up), then
 // the swizzled f16 matrices d0, d1, d2, dT, 2^-9 d1, 2^-9 d2, 2^-9 d0 of the
-// inverse N-point DFT, one after another along K (zero padded to 64 values).
+// inverse N-point DFT, NOUT rows each at the rows sl_mat_row gives (K zero
+// padded to 64 values).
 coll_status build_sliced_image(const HostTables& ht, int N, std::vector<unsigned char>* out) {
   if (N != 16 && N != 32) return COLL_EUNSUPPORTED;
   const int H = N / 2, nt = ht.n_terms;
   const int KP = 2 * N, NOUT = 2 * N;
   const size_t img_off = sliced_img_offset(N, nt);
-  const size_t img_bytes = size_t((kSlMats * KP + 63) / 64) * NOUT * 128;
+  const size_t img_bytes = size_t(kSlMats) * NOUT * 128;
   out->assign(img_off + img_bytes, 0);
   float* tab = reinterpret_cast<float*>(out->data());
   float* tmax = reinterpret_cast<float*>(out->data() + sliced_tmax_offset(N, nt));
@@ -735,9 +774,11 @@ coll_status build_sliced_image(const HostTables& ht, int N, std::vector<unsigned
   }
   unsigned char* img = out->data() + img_off;
   const double two_pi = 6.283185307179586476925286766559;
-  auto put = [&](int j, int kk, uint16_t val) {     // swizzled K-major position
-    const int kb = kk / 64, e = kk % 64, chunk = e / 8, within = e % 8;
-    const size_t off = size_t(kb) * NOUT * 128 + size_t(j) * 128 + size_t((chunk ^ (j & 7)) * 16) + size_t(within) * 2;
+  // matrix s, output row j, K index kk: row sl_mat_row(s) + j of the image
+  // (128-byte swizzled K-major rows, K zero padded to 64 values)
+  auto put = [&](int s, int j, int kk, uint16_t val) {
+    const int row = sl_mat_row(s, NOUT) + j, chunk = kk / 8, within = kk % 8;
+    const size_t off = size_t(row) * 128 + size_t((chunk ^ (row & 7)) * 16) + size_t(within) * 2;
     std::memcpy(img + off, &val, 2);
   };
   for (int j = 0; j < NOUT; ++j) {
@@ -754,7 +795,7 @@ coll_status build_sliced_image(const HostTables& ht, int N, std::vector<unsigned
       const double t2 = (t1 - d1) * 512.0, d2 = std::nearbyint(t2);
       const double dT = t2 - d2;
       const double m[kSlMats] = {d0, d1, d2, dT, d1 / 512.0, d2 / 512.0, d0 / 512.0};
-      for (int s = 0; s < kSlMats; ++s) put(j, s * KP + kk, sl_half_bits(m[s]));
+      for (int s = 0; s < kSlMats; ++s) put(s, j, kk, sl_half_bits(m[s]));
     }
   }
   return COLL_OK;

@@ -115,6 +115,10 @@ __device__ __forceinline__ void tld8_wait(uint32_t (&a)[8], uint32_t (&b)[8], ui
                :
                : "memory");
 }
+// ties the registers of an 8-column load to a wait issued just before (no instruction)
+__device__ __forceinline__ void tld8_tie(uint32_t (&v)[8]) {
+  asm volatile("" : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]) :: "memory");
+}
 // wait for the tensor-memory loads in flight; the registers of v are tied to the
 // wait so that no use of them is scheduled before it
 __device__ __forceinline__ void tld_wait(uint32_t (&v)[16]) {
