@@ -52,6 +52,7 @@ def fp64_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
 KERNEL_SOURCES = {
     "collision_f64_n32": ["collision_impl.cuh", "collision_layout.cuh", "fft.cuh", "twiddles.h", "coll_inst_d32.cu"],
     "moments_f64": ["moments.cu"],
+    "conservation_f64": ["moments.cu"],
     "mixed_f16_n32": ["mixed.cu", "tcgen05.cuh"],
     "mixed_sliced_n32": ["sliced.cu", "tcgen05.cuh", "dfloat.cuh"],
     "m2d_f64_n32": ["m2d_impl.cuh", "m2d_d.cu", "fft.cuh", "twiddles.h"],
@@ -778,7 +779,7 @@ def run_ours(args, rank, world, local_rank):
                          "ms_per_launch": cons_ms, "achieved_gbs": cons_bytes / (cons_ms / 1e3) / 1e9,
                          "peak_gbs": peaks.get("hbm_gbs"),
                          "frac": (cons_bytes / (cons_ms / 1e3) / 1e9 / peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None,
-                         "bytes_per_launch": cons_bytes, "bound": "hbm",
+                         "bytes_per_launch": cons_bytes, "bound": "hbm", "traffic": load_traffic("conservation_f64"),
                          "rel_max_fp64": cons64},
     }
     if world > 1:
