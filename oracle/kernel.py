@@ -46,6 +46,7 @@ class Params:
     Mr: int = 16              # radial GL nodes on [0, R]
     sphere_rule: int = 0
     dealias: int = 0
+    rank: int = 0             # lam != 1: radial terms per direction (0: the Mr node terms; see radial_factors)
 
     @property
     def support(self) -> float:
@@ -194,7 +195,48 @@ def direction_terms(p: Params, xv: np.ndarray, ep: np.ndarray, wp: float,
         Psi = psi_general_cheb(su, rho, p.R, p.lam)[inv]
     else:
         Psi = psi_general(su, rho, p.R, p.lam)[inv]   # [n, Mr]
-    return [(4.0 * b0 * wp, 2.0 * W[i] * rho[i] * cosm[:, i], Psi[:, i]) for i in range(p.Mr)]
+    full = [(4.0 * b0 * wp, 2.0 * W[i] * rho[i] * cosm[:, i], Psi[:, i]) for i in range(p.Mr)]
+    fac = radial_factors(p, rho, W)
+    if fac is None:
+        return full
+    P, Rm = fac
+    A = np.stack([t[1] for t in full], axis=1)         # [n, Mr]: a_i cos(rho_i t)
+    return [(4.0 * b0 * wp, A @ P[q], Psi @ Rm[q]) for q in range(P.shape[0])]
+
+
+def radial_factors(p: Params, rho: np.ndarray, W: np.ndarray):
+    """Low-rank separable approximation of the radial kernel (lam != 1).
+
+    Per direction the Mr radial terms sum to
+        sum_i a_i cos(rho_i t) Psi_{rho_i}(s),   a_i = 2 W_i rho_i,
+        Psi_rho(s) = int_0^R g_rho(r) J0(r s) dr,  g_rho(r) = 2 pi r (rho^2 + r^2)^{(lam-1)/2},
+    a bilinear form in the Mr-vectors c(t) = cos(rho_i t) and a_i Psi_{rho_i}(s)
+    through the kernel matrix of B~ on (rho_i, r).  Its singular vectors are the
+    eigenvectors U of the Gram matrix G_ii' = a_i a_i' int_0^R g_i g_i' dr (an
+    integral, independent of the quadrature that evaluates it); keeping the r
+    largest, term q of a direction is
+        alpha_q  = sqrt(s_q) sum_i U_iq cos(rho_i t)
+        alpha'_q = sum_i U_iq a_i Psi_{rho_i}(s) / sqrt(s_q),   s_q = sqrt(eigenvalue q),
+    so sum_q alpha_q alpha'_q = c^T U_r U_r^T diag(a) Psi, exact for r = Mr.
+    Every term keeps the form alpha(xi . e) alpha'(|xi_perp|) with alpha even,
+    so the loss built from the same terms keeps mass exact.
+    Returns (P, Rm) with alpha_q = sum_i P[q, i] (a_i cos(rho_i t)) and
+    alpha'_q = sum_i Rm[q, i] Psi_{rho_i}(s), or None (rank 0, or lam = 1) for the
+    Mr node terms themselves; rank = Mr gives the same operator in the
+    rotated basis."""
+    if p.lam == 1.0 or p.rank <= 0:
+        return None
+    r, w = _psi_nodes(float(np.min(rho)), p.R)
+    a = 2.0 * W * rho
+    g = (2.0 * math.pi) * r[:, None] * (rho[None, :] ** 2 + r[:, None] ** 2) ** ((p.lam - 1.0) / 2.0)   # [nr, Mr]
+    G = a[:, None] * a[None, :] * ((w[:, None] * g).T @ g)            # [Mr, Mr]
+    ev, U = np.linalg.eigh(G)
+    order = np.argsort(ev)[::-1][:min(p.rank, p.Mr)]
+    ev, U = ev[order], U[:, order]
+    sq = np.sqrt(np.sqrt(ev))                                          # sqrt(s_q)
+    P = (sq[:, None] * U.T) / a[None, :]
+    Rm = (U.T * a[None, :]) / sq[:, None]
+    return P, Rm
 
 
 def rules(p: Params):
