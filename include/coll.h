@@ -98,6 +98,21 @@ typedef enum {
  *            GPU; 1 returns COLL_EUNSUPPORTED)
  *   prec     compute precision of the transforms (coll_precision)
  *   io_dtype 0: f and Q are double; 1: f and Q are float
+ *   rank     lambda != 1 only: 0 (default) keeps one term per direction and
+ *            radial node (M/2 x Mr gain terms); 1 <= rank <= Mr keeps `rank`
+ *            terms per direction, the low-rank separable approximation of the
+ *            radial kernel B~(|x|, |y|) (the separated kernel of sec. 4.4.1 in
+ *            its SVD form: the eigenvectors of the Gram matrix
+ *            G_ii' = a_i a_i' int_0^R g_i g_i' dr, a_i = 2 W_i rho_i,
+ *            g_i(r) = 2 pi r (rho_i^2 + r^2)^((lambda-1)/2), largest first);
+ *            mass stays exact for every rank; rank = Mr is the full operator.
+ *            The factors are the singular vectors of the radial kernel
+ *            factor (long double one-sided Jacobi at plan time), each
+ *            determined to rounding over its gap to the next singular value.
+ *            At lambda = 0, Mr = 8 the relative L2 distance to rank 0 is about
+ *            2e-4 at rank 4, 8e-5 at rank 5, 1e-6 at rank 6, 1e-9 at rank 7.
+ *            Ignored for lambda = 1 (one term per direction already).
+ *            COLL_EINVAL outside 0 .. Mr.
  */
 typedef struct {
   int32_t N;
@@ -112,6 +127,7 @@ typedef struct {
   int32_t dealias;
   int32_t prec;
   int32_t io_dtype;
+  int32_t rank;
 } coll_plan_desc;
 
 /*

@@ -34,7 +34,8 @@ class coll_plan_desc(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("L", ctypes.c_double), ("S", ctypes.c_double),
                 ("lambda_", ctypes.c_double), ("b0", ctypes.c_double), ("M", ctypes.c_int32),
                 ("Mtheta", ctypes.c_int32), ("Mr", ctypes.c_int32), ("sphere_rule", ctypes.c_int32),
-                ("dealias", ctypes.c_int32), ("prec", ctypes.c_int32), ("io_dtype", ctypes.c_int32)]
+                ("dealias", ctypes.c_int32), ("prec", ctypes.c_int32), ("io_dtype", ctypes.c_int32),
+                ("rank", ctypes.c_int32)]
 
 
 class coll_m2d_plan_desc(ctypes.Structure):
@@ -141,12 +142,12 @@ def _ptr(t):
 
 
 def make_desc(N, L, S=0.0, lam=1.0, b0=-1.0, M=48, Mtheta=4, Mr=16, sphere_rule=0, dealias=0, prec="f64",
-              io_dtype=None) -> coll_plan_desc:
+              io_dtype=None, rank=0) -> coll_plan_desc:
     p = PREC[prec] if isinstance(prec, str) else int(prec)
     if io_dtype is None:
         io_dtype = 1 if p == COLL_F32 else 0
     return coll_plan_desc(int(N), float(L), float(S), float(lam), float(b0), int(M), int(Mtheta), int(Mr),
-                          int(sphere_rule), int(dealias), p, int(io_dtype))
+                          int(sphere_rule), int(dealias), p, int(io_dtype), int(rank))
 
 
 def coll_plan_create(desc: coll_plan_desc) -> int:
@@ -341,9 +342,9 @@ class Plan:
     """RAII wrapper: a plan, its workspace sized for max_cells, and eval helpers."""
 
     def __init__(self, N, L, S=0.0, lam=1.0, b0=-1.0, M=48, Mtheta=4, Mr=16, sphere_rule=0, prec="f64",
-                 io_dtype=None, max_cells=1, device=None):
+                 io_dtype=None, max_cells=1, device=None, rank=0):
         import torch
-        self.desc = make_desc(N, L, S, lam, b0, M, Mtheta, Mr, sphere_rule, 0, prec, io_dtype)
+        self.desc = make_desc(N, L, S, lam, b0, M, Mtheta, Mr, sphere_rule, 0, prec, io_dtype, rank)
         self.N = int(N)
         self.io_dtype = self.desc.io_dtype
         self.torch_dtype = torch.float64 if self.io_dtype == 0 else torch.float32

@@ -155,7 +155,7 @@ coll_status coll_plan_create(const coll_plan_desc* desc, coll_plan* out) {
   if (!desc || !out) return COLL_EINVAL;
   const coll_plan_desc d = *desc;
   if (!(d.L > 0) || !std::isfinite(d.L) || d.S < 0 || !(d.lambda >= 0 && d.lambda <= 1) || d.M <= 0 ||
-      d.Mtheta <= 0 || d.Mr <= 0 || d.Mr > 256 || (d.io_dtype != 0 && d.io_dtype != 1) ||
+      d.Mtheta <= 0 || d.Mr <= 0 || d.Mr > 256 || d.rank < 0 || d.rank > d.Mr || (d.io_dtype != 0 && d.io_dtype != 1) ||
       (d.sphere_rule != 0 && d.sphere_rule != 1) || (d.dealias != 0 && d.dealias != 1))
     return COLL_EINVAL;
   if (d.prec != COLL_F64 && d.prec != COLL_F32 && d.prec != COLL_MIXED_F16X2 && d.prec != COLL_MIXED_BF16X3 &&
@@ -237,7 +237,8 @@ coll_status coll_plan_tables_host(const coll_plan_desc* desc, double* out, size_
                                   size_t* n_doubles) {
   if (!desc || !n_terms || !n_doubles) return COLL_EINVAL;
   const coll_plan_desc d = *desc;
-  if (!(d.L > 0) || d.M <= 0 || d.Mtheta <= 0 || d.Mr <= 0 || d.N < 4 || d.N % 2) return COLL_EINVAL;
+  if (!(d.L > 0) || d.M <= 0 || d.Mtheta <= 0 || d.Mr <= 0 || d.N < 4 || d.N % 2 || d.rank < 0 || d.rank > d.Mr)
+    return COLL_EINVAL;
   HostTables ht;
   const coll_status st = build_tables(d, &ht);
   if (st != COLL_OK) return st;

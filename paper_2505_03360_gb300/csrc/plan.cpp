@@ -16,7 +16,9 @@
 // lambda = 1: Psi = 2 pi R J1(R s) / s, one term per direction with
 // alpha_p = sum_i alpha_{p,i}.  lambda != 1: Psi_{rho_i} is interpolated in s
 // by piecewise Chebyshev series (unit panels, degree 47) whose samples come
-// from composite Gauss-Legendre quadrature in r, graded near r = 0.
+// from composite Gauss-Legendre quadrature in r, graded near r = 0; with a
+// rank r > 0 the Mr node terms of a direction are replaced by r combinations
+// of them (RadialFactors, the low-rank separable form of the radial kernel).
 //
 // Quadrature nodes are computed here by Newton iteration on the Legendre
 // recurrence in long double.
@@ -204,6 +206,97 @@ struct PsiCheb {
   }
 };
 
+// Low-rank separable form of the radial sum (lambda != 1, rank r): per
+// direction the Mr node terms give sum_i a_i cos(rho_i t) Psi_{rho_i}(s),
+// a_i = 2 W_i rho_i, Psi_rho(s) = int_0^R g_rho(r) J0(r s) dr,
+// g_rho(r) = 2 pi r (rho^2 + r^2)^((lambda-1)/2).  With U the eigenvectors of
+// the Gram matrix G_ii' = a_i a_i' int_0^R g_i g_i' dr (largest eigenvalues
+// first, e_q) and s_q = sqrt(e_q), term q is
+//   alpha_q = sum_i P[q][i] a_i cos(rho_i t),  P[q][i] = sqrt(s_q) U_iq / a_i
+//   alpha'_q = sum_i Rm[q][i] Psi_{rho_i}(s),  Rm[q][i] = U_iq a_i / sqrt(s_q)
+// so that sum_q alpha_q alpha'_q = c^T U_r U_r^T diag(a) Psi (exact for r = Mr).
+// U and s_q are the left singular vectors and singular values of the factor
+// Y_ik = a_i g_i(r_k) sqrt(w_k) (G = Y Y^T) on the composite Gauss-Legendre
+// rule of PsiCheb, by one-sided Jacobi rotations in long double: the
+// subspace of the r largest is accurate to rounding over s_r - s_{r+1}.
+struct RadialFactors {
+  int rank = 0, Mr = 0;
+  std::vector<double> P, Rm;   // [rank][Mr]
+
+  void build(const std::vector<double>& rho, const std::vector<double>& W, double R, double lam, int r_keep) {
+    Mr = int(rho.size());
+    rank = r_keep;
+    double rmin = rho[0];
+    for (double v : rho) rmin = std::min(rmin, v);
+    std::vector<double> r, w;
+    radial_panels(rmin, R, &r, &w);
+    // Y_ik = a_i g_i(r_k) sqrt(w_k), so that Y Y^T = G; one-sided Jacobi
+    // rotations of the rows of Y until they are orthogonal: Y = U diag(s) V^T
+    // with U the accumulated rotations and s the final row norms (the
+    // eigenvectors of G without squaring its condition number)
+    const size_t nr = r.size();
+    std::vector<long double> a(Mr), Y(size_t(Mr) * nr), U(size_t(Mr) * Mr, 0.0L);
+    for (int i = 0; i < Mr; ++i) a[i] = 2.0L * W[i] * rho[i];
+    for (int i = 0; i < Mr; ++i)
+      for (size_t k = 0; k < nr; ++k)
+        Y[size_t(i) * nr + k] = a[i] * 2.0L * kPiL * r[k] *
+                                powl((long double)rho[i] * rho[i] + (long double)r[k] * r[k],
+                                     0.5L * ((long double)lam - 1.0L)) *
+                                sqrtl((long double)w[k]);
+    for (int i = 0; i < Mr; ++i) U[size_t(i) * Mr + i] = 1.0L;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+      bool rotated = false;
+      for (int p = 0; p < Mr; ++p)
+        for (int q = p + 1; q < Mr; ++q) {
+          long double al = 0.0L, be = 0.0L, ga = 0.0L;
+          for (size_t k = 0; k < nr; ++k) {
+            const long double yp = Y[size_t(p) * nr + k], yq = Y[size_t(q) * nr + k];
+            al += yp * yp;
+            be += yq * yq;
+            ga += yp * yq;
+          }
+          if (fabsl(ga) <= 1e-19L * sqrtl(al * be)) continue;
+          rotated = true;
+          const long double zeta = (be - al) / (2.0L * ga);
+          const long double t = (zeta >= 0 ? 1.0L : -1.0L) / (fabsl(zeta) + sqrtl(1.0L + zeta * zeta));
+          const long double c = 1.0L / sqrtl(1.0L + t * t), sn = c * t;
+          for (size_t k = 0; k < nr; ++k) {
+            const long double yp = Y[size_t(p) * nr + k], yq = Y[size_t(q) * nr + k];
+            Y[size_t(p) * nr + k] = c * yp - sn * yq;
+            Y[size_t(q) * nr + k] = sn * yp + c * yq;
+          }
+          for (int k = 0; k < Mr; ++k) {
+            const long double up = U[size_t(k) * Mr + p], uq = U[size_t(k) * Mr + q];
+            U[size_t(k) * Mr + p] = c * up - sn * uq;
+            U[size_t(k) * Mr + q] = sn * up + c * uq;
+          }
+        }
+      if (!rotated) break;
+    }
+    std::vector<long double> sv(Mr, 0.0L);
+    for (int i = 0; i < Mr; ++i) {
+      long double acc = 0.0L;
+      for (size_t k = 0; k < nr; ++k) acc += Y[size_t(i) * nr + k] * Y[size_t(i) * nr + k];
+      sv[i] = sqrtl(acc);
+    }
+    std::vector<int> order(Mr);
+    for (int i = 0; i < Mr; ++i) order[i] = i;
+    for (int i = 1; i < Mr; ++i)                  // singular values descending
+      for (int j = i; j > 0 && sv[order[j]] > sv[order[j - 1]]; --j) std::swap(order[j], order[j - 1]);
+    P.assign(size_t(rank) * Mr, 0.0);
+    Rm.assign(size_t(rank) * Mr, 0.0);
+    for (int q = 0; q < rank; ++q) {
+      const int col = order[q];
+      const long double sq = sqrtl(sv[col]);
+      for (int i = 0; i < Mr; ++i) {
+        const long double u = U[size_t(i) * Mr + col];
+        P[size_t(q) * Mr + i] = double(sq * u / a[i]);
+        Rm[size_t(q) * Mr + i] = double(u * a[i] / sq);
+      }
+    }
+  }
+};
+
 double psi_hs(double s, double R) {
   if (s * R < 1e-8) return double(kPiL) * R * R;
   return 2.0 * double(kPiL) * R * std::cyl_bessel_j(1.0, R * s) / s;
@@ -227,7 +320,8 @@ coll_status build_tables(const coll_plan_desc& d, HostTables* out) {
     W[i] = 0.5 * R * wr[i];
   }
   const bool hs = (lam == 1.0);
-  const int per_dir = hs ? 1 : d.Mr;
+  const bool lowrank = !hs && d.rank > 0;
+  const int per_dir = hs ? 1 : (lowrank ? d.rank : d.Mr);
   const int n_terms = int(dirs.size()) * per_dir + 1;
   const size_t plane = size_t(N) * N * H;
   out->n_terms = n_terms;
@@ -237,9 +331,11 @@ coll_status build_tables(const coll_plan_desc& d, HostTables* out) {
   auto kval = [N](int idx) { return idx < N / 2 ? idx : idx - N; };
 
   PsiCheb cheb;
+  RadialFactors rf;
   if (!hs) {
     const double kmax = dk * (N / 2);
     cheb.build(rho, R, lam, std::sqrt(3.0) * kmax + 1e-9);
+    if (lowrank) rf.build(rho, W, R, lam, d.rank);
   }
   std::vector<double> Lam(plane, 0.0);
 
@@ -262,11 +358,27 @@ coll_status build_tables(const coll_plan_desc& d, HostTables* out) {
             double* t = &out->tab[(size_t(p) * plane + idx) * 2];
             t[0] = cp * a;
             t[1] = b;
-          } else {
+          } else if (!lowrank) {
             for (int i = 0; i < d.Mr; ++i) {
               const double a = 2.0 * W[i] * rho[i] * std::cos(rho[i] * proj);
               const double b = cheb.eval(i, s);
               double* t = &out->tab[((size_t(p) * per_dir + i) * plane + idx) * 2];
+              t[0] = cp * a;
+              t[1] = b;
+            }
+          } else {
+            double av[256], bv[256];
+            for (int i = 0; i < d.Mr; ++i) {
+              av[i] = 2.0 * W[i] * rho[i] * std::cos(rho[i] * proj);
+              bv[i] = cheb.eval(i, s);
+            }
+            for (int q = 0; q < d.rank; ++q) {
+              double a = 0.0, b = 0.0;
+              for (int i = 0; i < d.Mr; ++i) {
+                a += rf.P[size_t(q) * d.Mr + i] * av[i];
+                b += rf.Rm[size_t(q) * d.Mr + i] * bv[i];
+              }
+              double* t = &out->tab[((size_t(p) * per_dir + q) * plane + idx) * 2];
               t[0] = cp * a;
               t[1] = b;
             }

@@ -25,10 +25,10 @@ def test_status_strings():
     assert "unknown" in coll.coll_status_string(99)
 
 
-def _compare_tables(N, L, lam, M, Mt, Mr, rule=0, S=0.0, tol=1e-13):
-    desc = coll.make_desc(N, L, S=S, lam=lam, M=M, Mtheta=Mt, Mr=Mr, sphere_rule=rule, prec="f64")
+def _compare_tables(N, L, lam, M, Mt, Mr, rule=0, S=0.0, tol=1e-13, rank=0):
+    desc = coll.make_desc(N, L, S=S, lam=lam, M=M, Mtheta=Mt, Mr=Mr, sphere_rule=rule, prec="f64", rank=rank)
     tab = coll.coll_plan_tables_host(desc)
-    p = Params(N=N, L=L, S=S, lam=lam, M=M, Mtheta=Mt, Mr=Mr, sphere_rule=rule)
+    p = Params(N=N, L=L, S=S, lam=lam, M=M, Mtheta=Mt, Mr=Mr, sphere_rule=rule, rank=rank)
     m = multipliers(p)
     H = N // 2
     n3 = float(N) ** 3
@@ -41,6 +41,10 @@ def _compare_tables(N, L, lam, M, Mt, Mr, rule=0, S=0.0, tol=1e-13):
         B[nyq] = 0
         sig = np.abs(tab[t, ..., 1]).max() / np.abs(B).max()        # the balancing power of two
         assert abs(math.log2(sig) - round(math.log2(sig))) < 1e-9
+        if rank:
+            # a low-rank term is defined up to a common sign of its two factors
+            # (the sign of an eigenvector); the product is not
+            sig *= np.sign(np.sum(tab[t, ..., 1] * B))
         sa = np.abs(A).max()
         sb = np.abs(B).max()
         assert np.abs(tab[t, ..., 0] * sig - A).max() <= tol * sa, t
@@ -68,10 +72,24 @@ def test_tables_paper_rule_and_N24():
     _compare_tables(24, 8.0, 1.0, 32, 4, 8, rule=1, S=3.3)
 
 
+@pytest.mark.parametrize("rank", [3, 5, 6])
+def test_tables_low_rank_maxwell(rank):
+    """lambda = 0, rank r: the host tables equal the oracle's low-rank terms
+    (own one-sided Jacobi SVD in long double against numpy's).  A term's
+    singular vector is determined to rounding over the gap to the next
+    singular value; at Mr = 8 the gaps after the sixth value are small
+    (s_7 / s_1 = 3e-5), so terms 7 and 8 agree only to about 1e-10 and are
+    not compared term by term."""
+    _compare_tables(16, (3 + math.sqrt(2)) * 3, 0.0, 32, 4, 8, S=6.0, tol=1e-11, rank=rank)
+
+
 def test_tables_reject_bad_desc():
     bad = coll.make_desc(16, 8.0, M=30, Mtheta=4)      # Mphi odd
     with pytest.raises(coll.CollError):
         coll.coll_plan_tables_host(bad)
+    for rank in (-1, 9):                                 # outside 0 .. Mr
+        with pytest.raises(coll.CollError):
+            coll.coll_plan_tables_host(coll.make_desc(16, 8.0, lam=0.0, M=32, Mtheta=4, Mr=8, rank=rank))
 
 
 @pytest.mark.parametrize("N,L,A,S", [(16, 8.0, 8, 0.0), (32, 10.0, 16, 3.5), (64, 8.0, 5, 0.0)])
