@@ -217,6 +217,8 @@ def radial_factors(p: Params, rho: np.ndarray, W: np.ndarray):
     largest, term q of a direction is
         alpha_q  = sqrt(s_q) sum_i U_iq cos(rho_i t)
         alpha'_q = sum_i U_iq a_i Psi_{rho_i}(s) / sqrt(s_q),   s_q = sqrt(eigenvalue q),
+    (U and s_q from the singular value decomposition of the factor
+    Y_ik = a_i g_i(r_k) sqrt(w_k), G = Y Y^T, on the radial quadrature of Psi),
     so sum_q alpha_q alpha'_q = c^T U_r U_r^T diag(a) Psi, exact for r = Mr.
     Every term keeps the form alpha(xi . e) alpha'(|xi_perp|) with alpha even,
     so the loss built from the same terms keeps mass exact.
@@ -229,11 +231,13 @@ def radial_factors(p: Params, rho: np.ndarray, W: np.ndarray):
     r, w = _psi_nodes(float(np.min(rho)), p.R)
     a = 2.0 * W * rho
     g = (2.0 * math.pi) * r[:, None] * (rho[None, :] ** 2 + r[:, None] ** 2) ** ((p.lam - 1.0) / 2.0)   # [nr, Mr]
-    G = a[:, None] * a[None, :] * ((w[:, None] * g).T @ g)            # [Mr, Mr]
-    ev, U = np.linalg.eigh(G)
-    order = np.argsort(ev)[::-1][:min(p.rank, p.Mr)]
-    ev, U = ev[order], U[:, order]
-    sq = np.sqrt(np.sqrt(ev))                                          # sqrt(s_q)
+    # Y Y^T = G with Y_ik = a_i g_i(r_k) sqrt(w_k): the left singular vectors of Y
+    # are the eigenvectors of G, computed without squaring its condition number
+    Y = a[:, None] * (g * np.sqrt(w)[:, None]).T                       # [Mr, nr]
+    U, sv, _ = np.linalg.svd(Y, full_matrices=False)
+    k = min(p.rank, p.Mr)
+    U, sv = U[:, :k], sv[:k]
+    sq = np.sqrt(sv)                                                   # sqrt(s_q)
     P = (sq[:, None] * U.T) / a[None, :]
     Rm = (U.T * a[None, :]) / sq[:, None]
     return P, Rm
