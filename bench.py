@@ -441,6 +441,36 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def time_lowrank(torch, coll, synth, dev, w, n=1024):
+    """Maxwell molecules (lambda = 0, Mr = 8) on n FP32 N = 32 bimodal cells: the
+    full radial sum against the low-rank separable kernel at ranks 6, 5, 4
+    (ms per launch; relative L2 of the batch against the full operator)."""
+    N = w["N"]
+    f = synth.bimodal_batch_device(n, N, w["L"], 21, dtype=torch.float32, device=dev)
+    out, ref = {}, None
+    for rank in (0, 6, 5, 4):
+        plan = coll.Plan(N, w["L"], lam=0.0, M=w["M"], Mtheta=w["Mtheta"], Mr=8, prec="f32", max_cells=n,
+                         device=dev, rank=rank)
+        Q = torch.empty_like(f)
+        plan.eval(f, Q)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(3):
+            plan.eval(f, Q)
+        b.record()
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / 3
+        if ref is None:
+            ref = Q.double()
+        out["rank%d" % rank if rank else "full"] = {
+            "terms": plan.n_terms, "ms_per_launch": ms, "cell_evals_per_s": n / (ms / 1e3),
+            "rel_l2_vs_full": float(torch.linalg.vector_norm(Q.double() - ref) / torch.linalg.vector_norm(ref))}
+        plan.close()
+    return {"workload": "%d FP32 cells, N = 32, lambda = 0, M = 48, Mr = 8 (24 directions x 8 radial nodes), "
+                        "bimodal Maxwellians" % n, **out}
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -910,6 +940,8 @@ def run_ours(args, rank, world, local_rank):
         "cell_evals_per_s": rg["cells"] / (rg["ms"] / 1e3), "status": rg["status"],
         "roofline": {"bound": "alu", "achieved": rg_tf, "peak": p32, "unit": "TFLOP/s", "frac": rg_tf / p32,
                      "peak_basis": "FP32 pipe (as the 2D FP32 line)", "flops_per_launch": rg["flops"]}}
+    # low-rank radial kernel for Maxwell molecules (plan rank): FP32, N = 32, M = 48, Mr = 8
+    line["lowrank"] = time_lowrank(torch, coll, synth, dev, w)
     if args.serve_requests > 0:
         from paper_2505_03360_gb300.service import Service, stream_jobs
         svc = Service(hbm_budget_bytes=120e9, device=str(dev), max_wall_s=args.serve_max_wall)

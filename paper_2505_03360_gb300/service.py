@@ -52,13 +52,21 @@ def effective_precision(precision: str, N: int) -> str:
     return precision
 
 
+# Maxwell-molecule requests run the low-rank radial kernel (plan rank) at the
+# largest rank whose approximation error stays well inside the class's own
+# error: 5 of 8 terms per direction for FP32 (8e-5 against the full operator,
+# FP32's own level is 5e-5 .. 5e-4), 7 for the sliced path (1e-9 against its
+# 1e-6 target).
+LAMBDA0_RANK = {"f32": 5, "mixed_sliced": 7}
+
+
 # relative GPU time per cell-evaluation by compute type (measured at N = 32, 25 terms)
 SPEED = {"f32": 1.0, "mixed_sliced": 3.2, "mixed_f16x2": 0.83, "f32x2": 7.6, "f64": 23.0}
 
 
 def cell_cost(N: int, lam: float, prec: str, M: int = 48, Mr: int = 8) -> float:
     """Relative cost of one cell-evaluation: terms x N^3 log2 N^3 x the compute type's speed."""
-    terms = M // 2 + 1 if lam == 1.0 else (M // 2) * Mr + 1
+    terms = M // 2 + 1 if lam == 1.0 else (M // 2) * (LAMBDA0_RANK.get(prec) or Mr) + 1
     return terms * N ** 3 * math.log2(N ** 3) * SPEED.get(prec, 1.0)
 
 
@@ -113,8 +121,9 @@ class Service:
         if key not in self.plans:
             Mr = 16 if lam == 1.0 else 8
             io = 1 if prec in ("f32",) + TENSOR else 0
+            rank = 0 if lam == 1.0 else LAMBDA0_RANK.get(prec, 0)
             self.plans[key] = coll.Plan(N, self.L, lam=lam, M=self.M, Mtheta=self.Mtheta, Mr=Mr, prec=prec,
-                                        io_dtype=io, max_cells=1, device=self.device)
+                                        io_dtype=io, max_cells=1, device=self.device, rank=rank)
         return self.plans[key]
 
     def _mix_plan(self, j, lane):
