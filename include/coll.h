@@ -94,8 +94,15 @@ typedef enum {
  *            azimuthal midpoints over a hemisphere (the paper's grid).
  *   Mr       Gauss-Legendre nodes of the radius |x| on [0, R]
  *   sphere_rule  0 (default) or 1, see above
- *   dealias  0: N-point circular products (the only mode implemented on the
- *            GPU; 1 returns COLL_EUNSUPPORTED)
+ *   dealias  0: N-point circular products (default).  1: Galerkin products:
+ *            f is interpolated spectrally onto the 3N/2 grid, the quadratic
+ *            terms are formed there (no aliasing into the modes |k_d| < N/2)
+ *            and Q is projected back onto those modes; the kernel runs on the
+ *            3N/2 grid, so each evaluation costs about (3/2)^3 log(3N/2)/log N
+ *            times more, plus six resampling passes.  Supported: COLL_F32 at
+ *            N = 16, 32; COLL_F64 and COLL_F32X2 at N = 16; otherwise
+ *            COLL_EUNSUPPORTED.  Not in ragged launches, coll_plan_autotune or
+ *            coll_eval_batch_static (COLL_EUNSUPPORTED).
  *   prec     compute precision of the transforms (coll_precision)
  *   io_dtype 0: f and Q are double; 1: f and Q are float
  *   rank     lambda != 1 only: 0 (default) keeps one term per direction and
@@ -145,7 +152,7 @@ coll_status coll_plan_create(const coll_plan_desc* desc, coll_plan* out);
 coll_status coll_plan_destroy(coll_plan plan);
 
 /* Number of separated terms T the plan evaluates per cell, including the loss
- * term (M/2 for lambda = 1, M/2 * Mr otherwise, plus 1). */
+ * term (M/2 for lambda = 1, M/2 * Mr otherwise (M/2 * rank with a rank), plus 1). */
 coll_status coll_plan_terms(coll_plan plan, int32_t* n_terms);
 
 /*
@@ -153,6 +160,9 @@ coll_status coll_plan_terms(coll_plan plan, int32_t* n_terms);
  * cells on the plan's device.  The workspace holds per-CTA scratch of the
  * persistent kernel (forward spectrum, transposed slabs, gain accumulator);
  * its size depends on the grid size, not on max_cells beyond the CTA count.
+ * In the Galerkin mode (dealias = 1) it also holds, per cell, f and Q on the
+ * 3N/2 grid and two complex resampling buffers of N (3N/2)^2 values, so it
+ * grows with max_cells (about 2.1 MB per FP32 cell at N = 32).
  */
 coll_status coll_workspace_size(coll_plan plan, int64_t max_cells, size_t* bytes);
 

@@ -342,9 +342,9 @@ class Plan:
     """RAII wrapper: a plan, its workspace sized for max_cells, and eval helpers."""
 
     def __init__(self, N, L, S=0.0, lam=1.0, b0=-1.0, M=48, Mtheta=4, Mr=16, sphere_rule=0, prec="f64",
-                 io_dtype=None, max_cells=1, device=None, rank=0):
+                 io_dtype=None, max_cells=1, device=None, rank=0, dealias=0):
         import torch
-        self.desc = make_desc(N, L, S, lam, b0, M, Mtheta, Mr, sphere_rule, 0, prec, io_dtype, rank)
+        self.desc = make_desc(N, L, S, lam, b0, M, Mtheta, Mr, sphere_rule, dealias, prec, io_dtype, rank)
         self.N = int(N)
         self.io_dtype = self.desc.io_dtype
         self.torch_dtype = torch.float64 if self.io_dtype == 0 else torch.float32

@@ -36,12 +36,28 @@ int grid_for(const coll_plan_s* p, int variant, long long n_cells) {
   return int(g);
 }
 
+// Galerkin mode: per cell the padded f and Q (Tio) and two complex scratch
+// buffers of the resampling (compute type), each slice 256-byte aligned
+struct GalerkinWs {
+  size_t pad_bytes, scr_bytes;
+};
+GalerkinWs galerkin_ws(const coll_plan_s* p, long long n_cells) {
+  const size_t es = p->io_f64 ? 8 : 4, cs = p->ctype == kCF32 ? 8 : 16;
+  const size_t n3 = size_t(p->Nk) * p->Nk * p->Nk;
+  auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+  return {r256(size_t(n_cells) * n3 * es), r256(size_t(n_cells) * galerkin_scratch_elems(p->d.N) * cs)};
+}
+
 // workspace that serves every variant (the autotuner may switch variants)
 size_t ws_need(const coll_plan_s* p, long long n_cells) {
   size_t b = 0;
   for (int v = 0; v < kVariants; ++v) {
     const size_t need = size_t(grid_for(p, v, n_cells)) * p->lay[v].ws_bytes_per_cta();
     b = need > b ? need : b;
+  }
+  if (p->galerkin) {
+    const GalerkinWs g = galerkin_ws(p, n_cells);
+    b = (b + 255) / 256 * 256 + 2 * g.pad_bytes + 2 * g.scr_bytes;
   }
   return b;
 }
@@ -71,6 +87,7 @@ coll_status ragged_prepare(const coll_cell_group* groups, const int64_t* cells, 
   for (int i = 0; i < n; ++i) {
     const coll_plan_s* p = groups[i].plan;
     if (!p || p->device != dev || cells[i] < 0) return COLL_EINVAL;
+    if (p->galerkin) return COLL_EUNSUPPORTED;          // ragged launches run N-point products only
     if (p->ctype != *ctype) return COLL_EUNSUPPORTED;
     if (p->io_f64 != want_io_f64) return COLL_EUNSUPPORTED;
     if (cells[i] > 0 && (!groups[i].f || !groups[i].Q || groups[i].f == groups[i].Q)) return COLL_EINVAL;
@@ -128,7 +145,27 @@ coll_status eval_variant(coll_plan_s* p, int v, const void* f, void* Q, int64_t 
   a.ws = ws;
   a.ws_per_cta = p->lay[v].ws_bytes_per_cta();
   a.status = p->status_dev;
-  const int e = launch_collision(p->d.N, p->ctype, p->io_f64, v, a, grid, stream);
+  if (!p->galerkin) {
+    const int e = launch_collision(p->Nk, p->ctype, p->io_f64, v, a, grid, stream);
+    return e == 0 ? COLL_OK : COLL_ECUDA;
+  }
+  // Galerkin mode: f -> f_pad, the kernel on the padded grid, Q_pad -> Q
+  if (!ws || !aligned256(ws)) return COLL_EINVAL;
+  if (ws_bytes < ws_need(p, n_cells)) return COLL_ENOMEM;
+  unsigned char* w = static_cast<unsigned char*>(ws) + (need + 255) / 256 * 256;
+  const GalerkinWs g = galerkin_ws(p, n_cells);
+  void* fpad = w;
+  void* qpad = w + g.pad_bytes;
+  void* sa = w + 2 * g.pad_bytes;
+  void* sb = w + 2 * g.pad_bytes + g.scr_bytes;
+  const bool cf64 = p->ctype != kCF32;
+  int e = launch_galerkin_resample(true, p->d.N, cf64, p->io_f64, f, fpad, sa, sb, n_cells, stream);
+  if (e == 0) {
+    a.f = fpad;
+    a.Q = qpad;
+    e = launch_collision(p->Nk, p->ctype, p->io_f64, v, a, grid, stream);
+  }
+  if (e == 0) e = launch_galerkin_resample(false, p->d.N, cf64, p->io_f64, qpad, Q, sa, sb, n_cells, stream);
   return e == 0 ? COLL_OK : COLL_ECUDA;
 }
 
@@ -161,21 +198,28 @@ coll_status coll_plan_create(const coll_plan_desc* desc, coll_plan* out) {
   if (d.prec != COLL_F64 && d.prec != COLL_F32 && d.prec != COLL_MIXED_F16X2 && d.prec != COLL_MIXED_BF16X3 &&
       d.prec != COLL_F32X2 && d.prec != COLL_MIXED_SLICED)
     return COLL_EINVAL;
-  if (d.dealias) return COLL_EUNSUPPORTED;
   const int ctype = d.prec == COLL_F64 ? kCF64
                   : d.prec == COLL_F32 ? kCF32
                   : d.prec == COLL_MIXED_F16X2 ? kCMixF16
                   : d.prec == COLL_MIXED_BF16X3 ? kCMixBF16
                   : d.prec == COLL_MIXED_SLICED ? kCMixSliced : kCDF;
   if (!valid_N(d.N, ctype)) return COLL_EUNSUPPORTED;
+  // Galerkin mode: the kernel runs on the 3N/2 grid (FP32: N = 16, 32; FP64 and
+  // float pairs: N = 16); the tensor-core paths have no padded grid
+  const int Nk = d.dealias ? 3 * d.N / 2 : d.N;
+  if (d.dealias && (is_mixed(ctype) || !valid_N(Nk, ctype) || !(d.N == 16 || d.N == 32))) return COLL_EUNSUPPORTED;
+  coll_plan_desc kd = d;
+  kd.N = Nk;
 
   HostTables ht;
-  coll_status st = build_tables(d, &ht);
+  coll_status st = build_tables(kd, &ht, d.dealias ? d.N : 0);
   if (st != COLL_OK) return st;
 
   coll_plan_s* p = new (std::nothrow) coll_plan_s();
   if (!p) return COLL_ENOMEM;
   p->d = d;
+  p->Nk = Nk;
+  p->galerkin = d.dealias != 0;
   p->ctype = ctype;
   p->io_f64 = d.io_dtype == 0;
   p->n_terms = ht.n_terms;
@@ -183,9 +227,9 @@ coll_status coll_plan_create(const coll_plan_desc* desc, coll_plan* out) {
   cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
   p->variant = 0;
   for (int v = 0; v < kVariants; ++v) {
-    if (!layout_info(d.N, ctype, v, &p->lay[v])) { delete p; return COLL_EUNSUPPORTED; }
+    if (!layout_info(Nk, ctype, v, &p->lay[v])) { delete p; return COLL_EUNSUPPORTED; }
     int per = 0;
-    if (collision_max_ctas_per_sm(d.N, ctype, p->io_f64, v, &per) != 0 || per < 1) {
+    if (collision_max_ctas_per_sm(Nk, ctype, p->io_f64, v, &per) != 0 || per < 1) {
       delete p;
       return COLL_ECUDA;
     }
@@ -285,6 +329,7 @@ coll_status coll_eval_batch(coll_plan p, const void* f, void* Q, int64_t n_cells
 coll_status coll_plan_autotune(coll_plan p, const void* f, void* Q, int64_t n_cells, void* ws, size_t ws_bytes,
                                coll_stream stream, int32_t* chosen) {
   if (!p || n_cells <= 0 || !f || !Q || f == Q) return COLL_EINVAL;
+  if (p->galerkin) return COLL_EUNSUPPORTED;
   if (ws_bytes < ws_need(p, n_cells)) return COLL_ENOMEM;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0, e1;

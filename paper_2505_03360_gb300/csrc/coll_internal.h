@@ -126,6 +126,11 @@ int sliced_max_ctas_per_sm(int N, bool io_f64, int* ctas);
 // Moments kernel (moments.cu)
 int launch_moments(const void* f, int io_f64, int N, double L, long long n_cells, double eta0,
                    double delta0, coll_moments* mom, uint8_t* mask, void* stream);
+// Galerkin mode (galerkin.cu): spectral resampling N^3 <-> (3N/2)^3 per cell,
+// through two complex scratch buffers of galerkin_scratch_elems(N) elements per cell
+size_t galerkin_scratch_elems(int N);
+int launch_galerkin_resample(bool to_pad, int N, bool compute_f64, bool io_f64, const void* in, void* out,
+                             void* sa, void* sb, long long n_cells, void* stream);
 // Collision invariants of Q per cell (moments.cu)
 int launch_conservation(const void* Q, int io_f64, int N, double L, long long n_cells, double* out, void* stream);
 
@@ -165,7 +170,9 @@ struct HostTables {
   int n_terms;
   std::vector<double> tab;    // [n_terms][N][N][N/2][2]
 };
-coll_status build_tables(const coll_plan_desc& d, HostTables* out);
+// mode_cut > 0: the tables of a grid of d.N points that carry only the modes
+// with every |k_d| < mode_cut / 2 (the Galerkin mode's padded grid)
+coll_status build_tables(const coll_plan_desc& d, HostTables* out, int mode_cut = 0);
 coll_status build_mixed_image(const HostTables& ht, int N, int parts, std::vector<unsigned char>* out);
 coll_status build_sliced_image(const HostTables& ht, int N, std::vector<unsigned char>* out);
 
@@ -186,6 +193,8 @@ struct coll_plan_s {
   int ctas_per_sm[coll::kVariants];
   int variant;                             // chosen by coll_plan_autotune (default 0)
   int num_sms;
+  int Nk;            // grid of the collision kernel: N, or 3N/2 in the Galerkin mode
+  bool galerkin;     // dealias = 1: products on the 3N/2 grid, result projected back
 };
 
 struct coll_m2d_plan_s {

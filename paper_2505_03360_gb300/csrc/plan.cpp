@@ -304,7 +304,7 @@ double psi_hs(double s, double R) {
 
 }  // namespace
 
-coll_status build_tables(const coll_plan_desc& d, HostTables* out) {
+coll_status build_tables(const coll_plan_desc& d, HostTables* out, int mode_cut) {
   const int N = d.N, H = N / 2;
   const double S = d.S > 0 ? d.S : 2.0 * d.L / (3.0 + std::sqrt(2.0));
   const double R = 2.0 * S;
@@ -329,6 +329,12 @@ coll_status build_tables(const coll_plan_desc& d, HostTables* out) {
   const double n3 = double(N) * N * N;
   const double dk = double(kPiL) / d.L;
   auto kval = [N](int idx) { return idx < N / 2 ? idx : idx - N; };
+  // modes kept: every |k_d| < N / 2, or < mode_cut / 2 on a padded grid
+  const int kcut = mode_cut > 0 ? mode_cut / 2 : N / 2;
+  auto kept = [&](int i0, int i1, int i2) {
+    const int a = kval(i0), b = kval(i1);
+    return (a < 0 ? -a : a) < kcut && (b < 0 ? -b : b) < kcut && i2 < kcut;
+  };
 
   PsiCheb cheb;
   RadialFactors rf;
@@ -346,7 +352,7 @@ coll_status build_tables(const coll_plan_desc& d, HostTables* out) {
       for (int i1 = 0; i1 < N; ++i1) {
         for (int i2 = 0; i2 < H; ++i2) {
           const size_t idx = (size_t(i0) * N + i1) * H + i2;
-          if (i0 == N / 2 || i1 == N / 2) continue;
+          if (i0 == N / 2 || i1 == N / 2 || !kept(i0, i1, i2)) continue;
           const double x0 = dk * kval(i0), x1 = dk * kval(i1), x2 = dk * i2;
           const double proj = x0 * dr.e[0] + x1 * dr.e[1] + x2 * dr.e[2];
           const double p0 = x0 - proj * dr.e[0], p1 = x1 - proj * dr.e[1], p2 = x2 - proj * dr.e[2];
@@ -408,7 +414,7 @@ coll_status build_tables(const coll_plan_desc& d, HostTables* out) {
     for (int i1 = 0; i1 < N; ++i1)
       for (int i2 = 0; i2 < H; ++i2) {
         const size_t idx = (size_t(i0) * N + i1) * H + i2;
-        if (i0 == N / 2 || i1 == N / 2) continue;
+        if (i0 == N / 2 || i1 == N / 2 || !kept(i0, i1, i2)) continue;
         last[2 * idx] = -Lam[idx];
         last[2 * idx + 1] = 1.0;
       }

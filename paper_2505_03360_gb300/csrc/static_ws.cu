@@ -54,6 +54,7 @@ extern "C" coll_status coll_eval_batch_static(coll_plan p, const void* f, void* 
   if (!p || n_cells < 0) return COLL_EINVAL;
   if (n_cells == 0) return COLL_OK;
   if (!f || !Q || f == Q) return COLL_EINVAL;
+  if (p->galerkin) return COLL_EUNSUPPORTED;    // the Galerkin mode's padded buffers scale with the batch
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return COLL_EINVAL;
   const int v = p->variant;
@@ -76,6 +77,6 @@ extern "C" coll_status coll_eval_batch_static(coll_plan p, const void* f, void* 
   a.ws = ws;
   a.ws_per_cta = per_cta;
   a.status = p->status_dev;
-  const int e = coll::launch_collision(p->d.N, p->ctype, p->io_f64, v, a, int(grid), stream);
+  const int e = coll::launch_collision(p->Nk, p->ctype, p->io_f64, v, a, int(grid), stream);
   return e == 0 ? COLL_OK : COLL_ECUDA;
 }

@@ -164,9 +164,10 @@ def test_api_errors_and_edges():
     with pytest.raises(coll.CollError) as e:
         coll.coll_plan_create(coll.make_desc(16, -1.0, prec="f64"))
     assert e.value.status == coll.COLL_EINVAL
-    with pytest.raises(coll.CollError) as e:
-        coll.coll_plan_create(coll.make_desc(16, L_CFG, prec="f64", dealias=1))
-    assert e.value.status == coll.COLL_EUNSUPPORTED
+    for N, prec in ((32, "f64"), (24, "f32"), (16, "mixed_sliced"), (32, "f32x2")):   # no padded-grid kernel
+        with pytest.raises(coll.CollError) as e:
+            coll.coll_plan_create(coll.make_desc(N, L_CFG, prec=prec, dealias=1))
+        assert e.value.status == coll.COLL_EUNSUPPORTED, (N, prec)
 
 
 def test_nonfinite_input_sets_sticky_status():
