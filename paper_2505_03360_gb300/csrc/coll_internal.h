@@ -28,15 +28,12 @@ struct LayoutInfo {
   int N, S0;
   bool w_smem, fh_smem, g_smem;
   int threads;
+  int cluster = 0;          // CTAs per cell (thread-block cluster), 0: one CTA per cell
   size_t w_bytes, fh_bytes, g_bytes;
-  size_t extra_ws = 0;      // global-only buffers (full-term spectrum and gain accumulator)
-  size_t smem_bytes() const {
-    return (w_smem ? w_bytes : 0) + (fh_smem ? fh_bytes : 0) + (g_smem ? g_bytes : 0);
-  }
-  size_t ws_bytes_per_cta() const {
-    size_t b = (w_smem ? 0 : w_bytes) + (fh_smem ? 0 : fh_bytes) + (g_smem ? 0 : g_bytes) + extra_ws;
-    return (b + 255) / 256 * 256;
-  }
+  size_t smem = 0;          // dynamic shared memory per CTA
+  size_t ws = 0;            // global workspace per CTA (the cluster form: a share of the cluster's)
+  size_t smem_bytes() const { return smem; }
+  size_t ws_bytes_per_cta() const { return (ws + 255) / 256 * 256; }
 };
 
 // compute types of the collision kernel

@@ -20,10 +20,12 @@ template <int N, typename T, int V> LayoutInfo make_info_v() {
   i.fh_smem = Cfg<N, T, V>::FH;
   i.g_smem = Cfg<N, T, V>::G;
   i.threads = kThreads;
+  i.cluster = Cfg<N, T, V>::CLUSTER;
   i.w_bytes = Ly::round16(Ly::W_BYTES);
   i.fh_bytes = Ly::round16(Ly::FH_BYTES);
   i.g_bytes = Ly::round16(Ly::G_BYTES);
-  i.extra_ws = Ly::round16(Ly::WG_BYTES) + Ly::round16(Ly::GG_BYTES);
+  i.smem = Ly::SMEM;
+  i.ws = Ly::WS;
   return i;
 }
 

@@ -34,6 +34,7 @@
 #include "coll_internal.h"
 #include "collision_layout.cuh"
 #include "fft.cuh"
+#include "tcgen05.cuh"
 
 namespace coll {
 
@@ -49,7 +50,8 @@ __device__ __forceinline__ bool finite_v(df x) { return isfinite(x); }
 
 enum PassMode : int { kPassF1 = 0, kPassFwd = 1, kPassInv = 2, kPassP3 = 3 };
 
-// One pass of length-N register FFTs over a set of pencils.  Pencil pid maps to
+// One pass of length-N register FFTs over a set of pencils (this thread's: p0,
+// p0 + pstep, ...; by default threadIdx.x in steps of the CTA).  Pencil pid maps to
 // (a, b) = (pid / inner, pid % inner) and starts at base + a*s_outer + b*s_inner;
 // its elements are s_elem apart.  Modes:
 //   kPassF1   two real rows of f packed into one complex FFT, split into the
@@ -62,11 +64,11 @@ enum PassMode : int { kPassF1 = 0, kPassFwd = 1, kPassInv = 2, kPassP3 = 3 };
 template <int N, typename T, typename Tio>
 __device__ __noinline__ bool run_pass(int mode, typename C2<T>::type* base, int count, int inner, int s_outer,
                                       int s_inner, int s_elem, int skip_b, const Tio* __restrict__ f, Tio* Q,
-                                      T* G, int s, int S0, int fh_row, bool last) {
+                                      T* G, int s, int S0, int fh_row, bool last, int p0 = -1, int pstep = kThreads) {
   using V2 = typename C2<T>::type;
   constexpr int H = N / 2;
   bool bad = false;
-  for (int pid = threadIdx.x; pid < count; pid += kThreads) {
+  for (int pid = p0 < 0 ? int(threadIdx.x) : p0; pid < count; pid += pstep) {
     const int a = pid / inner, b = pid % inner;
     if (mode == kPassInv && b == skip_b) continue;
     T xr[N], xi[N];
@@ -203,14 +205,15 @@ __device__ __noinline__ void run_p1(const typename C2<T>::type* __restrict__ tb,
 }
 
 // P1F: full axis-0 inverse of (A + iB) F for every full-spectrum pencil
-// (k1, k2) (no slab split), into the term buffer Wg[v0][k1][k2] (global).
+// (k1, k2) (no slab split; this thread's pencils as in run_pass), into the term
+// buffer Wg[v0][k1][k2] (global).
 template <int N, typename T, int V>
 __device__ __noinline__ void run_p1f(const typename C2<T>::type* __restrict__ tb, const typename C2<T>::type* Fh,
-                                     typename C2<T>::type* Wg) {
+                                     typename C2<T>::type* Wg, int p0 = -1, int pstep = kThreads) {
   using Ly = Lay<N, T, V>;
   using V2 = typename C2<T>::type;
   constexpr int H = Ly::H, FR = Ly::FH_ROW;
-  for (int pid = threadIdx.x; pid < N * N; pid += kThreads) {
+  for (int pid = p0 < 0 ? int(threadIdx.x) : p0; pid < N * N; pid += pstep) {
     const int k1 = pid / N, k2 = pid % N;
     T xr[N], xi[N];
     if (k2 == H || k1 == H) {
@@ -376,6 +379,11 @@ __device__ __noinline__ bool ragged_cell(const Tio* f, Tio* Q, const typename C2
   return bad;
 }
 
+// The body a ragged launch runs for variant V of (N, T): the cluster form needs a
+// cluster launch of its own, so its cells take the variant-0 body (the full first
+// pass, whose arithmetic it shares).
+template <int N, typename T, int V> constexpr int kRaggedV = Cfg<N, T, V>::CLUSTER > 0 ? 0 : V;
+
 // per-N body in the slab shape the group's plan uses (so that a ragged launch
 // equals coll_eval_batch of each group alone, whichever shape the autotuner chose)
 template <typename T, typename Tio, int N0, int... Ns>
@@ -383,7 +391,7 @@ struct RaggedDispatch<T, Tio, N0, Ns...> {
   static __device__ __forceinline__ void run(int N, int V, const Tio* f, Tio* Q, const typename C2<T>::type* tab,
                                              int nt, unsigned char* smem, unsigned char* wsc, bool& bad) {
     if (N == N0) {
-      if (V == 1) bad |= ragged_cell<N0, T, Tio, 1>(f, Q, tab, nt, smem, wsc);
+      if (V == 1) bad |= ragged_cell<N0, T, Tio, kRaggedV<N0, T, 1>>(f, Q, tab, nt, smem, wsc);
       else bad |= ragged_cell<N0, T, Tio, 0>(f, Q, tab, nt, smem, wsc);
     } else {
       RaggedDispatch<T, Tio, Ns...>::run(N, V, f, Q, tab, nt, smem, wsc, bad);
@@ -423,12 +431,12 @@ template <typename T, typename Tio, int... Ns>
 struct RaggedLaunch {
   static constexpr size_t smem() {      // the largest of every N's two slab shapes
     size_t m = 0;
-    for (size_t v : {Lay<Ns, T, 0>::SMEM..., Lay<Ns, T, 1>::SMEM...}) m = v > m ? v : m;
+    for (size_t v : {Lay<Ns, T, 0>::SMEM..., Lay<Ns, T, kRaggedV<Ns, T, 1>>::SMEM...}) m = v > m ? v : m;
     return m;
   }
   static constexpr size_t ws() {        // per CTA: 256-byte header + the largest scratch
     size_t m = 0;
-    for (size_t v : {Lay<Ns, T, 0>::WS..., Lay<Ns, T, 1>::WS...}) m = v > m ? v : m;
+    for (size_t v : {Lay<Ns, T, 0>::WS..., Lay<Ns, T, kRaggedV<Ns, T, 1>>::WS...}) m = v > m ? v : m;
     return 256 + (m + 255) / 256 * 256;
   }
   static int launch(const RaggedTable& t, void* wsp, size_t ws_per_cta, int grid, cudaStream_t st) {
@@ -446,20 +454,142 @@ struct RaggedLaunch {
   }
 };
 
+// ------------------------------------------------------------ cluster form
+// C CTAs of a thread-block cluster evaluate one cell together (Cfg::CLUSTER):
+// the full first pass with its global arrays shared by the cluster.  The
+// cluster's workspace holds the forward spectrum Fh and two term buffers Wg
+// (term t uses Wg[t mod 2]); every pass over Fh or Wg splits its pencils over
+// the C CTAs (CTA r takes pencils r T + i, r T + i + C T, ..., T threads per CTA),
+// and CTA r owns the slabs r SPC .. r SPC + SPC - 1 (SPC = S0 / C), whose gain
+// accumulators stay in its shared memory over all terms (no save and restore).
+// Per cell: F1, F2, F3 with a cluster barrier after each; per term P1F into
+// Wg[t mod 2], cluster barrier, then per own slab: copy the slab into shared
+// memory, axis 1, axis 2 with G += Re*Im (Q on the last term).
+// Ordering: P1F(t + 2) rewrites Wg[t mod 2] only after the barrier that follows
+// P1F(t + 1), which every CTA reaches after its slab copies of term t; the next
+// cell's F1 rewrites Fh only after the barrier that follows the last P1F.  Each
+// (pencil, slab) is computed by the same code as in the one-CTA full first pass,
+// so the results equal that form's bit for bit.
 template <int N, typename T, typename Tio, int V>
-int launch_one(const CollArgs& a, int grid, cudaStream_t st) {
+__device__ __forceinline__ void process_cell_cluster(const Tio* __restrict__ f, Tio* __restrict__ Q,
+                                                     const typename C2<T>::type* __restrict__ tab, int n_terms,
+                                                     unsigned char* smem, unsigned char* wcl, int r, bool& bad) {
+  using Ly = Lay<N, T, V>;
+  using V2 = typename C2<T>::type;
+  constexpr int C = Cfg<N, T, V>::CLUSTER;
+  constexpr int H = Ly::H, FR = Ly::FH_ROW, WR = Ly::W_ROW, NS = Ly::NS, SPC = Ly::SLABS_PER_CTA;
+  constexpr int GSLAB = NS * N * (N + 1);                 // elements of one slab of G
+  V2* W = reinterpret_cast<V2*>(smem);
+  T* G = reinterpret_cast<T*>(smem + Ly::round16(Ly::W_BYTES));
+  V2* Fh = reinterpret_cast<V2*>(wcl);
+  V2* Wg[2] = {reinterpret_cast<V2*>(wcl + Ly::round16(Ly::FH_BYTES)),
+               reinterpret_cast<V2*>(wcl + Ly::round16(Ly::FH_BYTES) + Ly::round16(Ly::WG_BYTES))};
+  const int p0 = r * kThreads + int(threadIdx.x), ps = C * kThreads;
+
+  run_pass<N, T, Tio>(kPassF1, Fh, N * N / 2, 1, 0, 0, 1, -1, f, Q, G, 0, 1, FR, false, p0, ps);
+  cluster_sync();
+  run_pass<N, T, Tio>(kPassFwd, Fh, N * H, H, N * FR, 1, FR, -1, f, Q, G, 0, 1, FR, false, p0, ps);
+  cluster_sync();
+  run_pass<N, T, Tio>(kPassFwd, Fh, N * H, H, FR, 1, N * FR, -1, f, Q, G, 0, 1, FR, false, p0, ps);
+  for (int i = threadIdx.x; i < SPC * GSLAB; i += kThreads) G[i] = T{};
+  cluster_sync();
+  for (int t = 0; t < n_terms; ++t) {
+    V2* Wt = Wg[t & 1];
+    run_p1f<N, T, V>(tab + size_t(t) * N * N * H, Fh, Wt, p0, ps);
+    cluster_sync();
+    const bool last = t == n_terms - 1;
+    for (int j = 0; j < SPC; ++j) {
+      const int s = r * SPC + j;                          // planes v0 = s NS .. s NS + NS - 1
+      const V2* src = Wt + size_t(s) * NS * N * N;
+      for (int i = threadIdx.x; i < NS * N * N; i += kThreads) {
+        const int m = i / (N * N), rem = i % (N * N);
+        cp_elem(W + (size_t(m) * N + rem / N) * WR + rem % N, src + i);
+      }
+      cp16_wait();
+      __syncthreads();
+      T* Gs = G + j * GSLAB;
+      run_pass<N, T, Tio>(kPassInv, W, NS * N, N, N * WR, 1, WR, H, f, Q, Gs, s * NS, 1, FR, false);
+      __syncthreads();
+      bad |= run_pass<N, T, Tio>(kPassP3, W, NS * N, N, N * WR, WR, 1, -1, f, Q, Gs, s * NS, 1, FR, last);
+      __syncthreads();
+    }
+  }
+}
+
+template <int N, typename T, typename Tio, int V>
+__global__ void __launch_bounds__(kThreads, 1) collision_cluster_kernel(CollArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int C = Cfg<N, T, V>::CLUSTER;
+  const int r = int(cluster_ctarank());
+  const long long first = blockIdx.x / C, step = gridDim.x / C;
+  // the cluster's workspace: its C consecutive per-CTA slices
+  unsigned char* wcl = static_cast<unsigned char*>(a.ws) + size_t(first) * C * a.ws_per_cta;
+  const auto* tab = static_cast<const typename C2<T>::type*>(a.tab);
+  bool bad = false;
+  for (long long c = first; c < a.n_cells; c += step) {       // the same cells for every CTA of a cluster
+    const Tio* f = static_cast<const Tio*>(a.f) + size_t(c) * N * N * N;
+    Tio* Q = static_cast<Tio*>(a.Q) + size_t(c) * N * N * N;
+    process_cell_cluster<N, T, Tio, V>(f, Q, tab, a.n_terms, smem, wcl, r, bad);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.status, kStatusNonFinite);
+}
+
+// Launch in clusters of C CTAs (one cell per cluster at a time).  `grid` is the
+// number of CTAs the caller's workspace covers (a.ws_per_cta each); the kernel
+// runs max(1, grid / C) clusters, capped at the cell count and at the number of
+// clusters that can be resident at once.
+template <int N, typename T, typename Tio, int V>
+int launch_cluster(const CollArgs& a, int grid, cudaStream_t st) {
+  constexpr int C = Cfg<N, T, V>::CLUSTER;
   constexpr size_t smem = Lay<N, T, V>::SMEM;
-  auto k = collision_kernel<N, T, Tio, V>;
+  auto k = collision_cluster_kernel<N, T, Tio, V>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return int(e);
-  k<<<grid, kThreads, smem, st>>>(a);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  long long clusters = grid / C < 1 ? 1 : grid / C;
+  if (clusters > a.n_cells) clusters = a.n_cells;
+  cfg.gridDim = dim3(C);
+  int resident = 0;
+  e = cudaOccupancyMaxActiveClusters(&resident, k, &cfg);
+  if (e != cudaSuccess) return int(e);
+  if (resident >= 1 && clusters > resident) clusters = resident;
+  cfg.gridDim = dim3(unsigned(C * clusters));
+  e = cudaLaunchKernelEx(&cfg, k, a);
+  if (e != cudaSuccess) return int(e);
   return int(cudaGetLastError());
+}
+
+template <int N, typename T, typename Tio, int V>
+int launch_one(const CollArgs& a, int grid, cudaStream_t st) {
+  if constexpr (Cfg<N, T, V>::CLUSTER > 0) {
+    return launch_cluster<N, T, Tio, V>(a, grid, st);
+  } else {
+    constexpr size_t smem = Lay<N, T, V>::SMEM;
+    auto k = collision_kernel<N, T, Tio, V>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return int(e);
+    k<<<grid, kThreads, smem, st>>>(a);
+    return int(cudaGetLastError());
+  }
 }
 
 template <int N, typename T, typename Tio, int V>
 int occupancy_one(int* ctas) {
   constexpr size_t smem = Lay<N, T, V>::SMEM;
-  auto k = collision_kernel<N, T, Tio, V>;
+  auto k = [] {
+    if constexpr (Cfg<N, T, V>::CLUSTER > 0) return collision_cluster_kernel<N, T, Tio, V>;
+    else return collision_kernel<N, T, Tio, V>;
+  }();
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return int(e);
   return int(cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k, kThreads, smem));

@@ -28,12 +28,26 @@ template <int N, typename T, int V = 0> struct Cfg;
     static constexpr int S0 = S0_;                                                         \
     static constexpr bool W = W_, FH = FH_, G = G_, FH_PAD = PAD_;                         \
     static constexpr bool P1F = false;                                                     \
+    static constexpr int CLUSTER = 0;                                                      \
   };
 #define COLL_CFG_P1F(N_, T_, V_, S0_, FH_, PAD_)                                           \
   template <> struct Cfg<N_, T_, V_> {                                                     \
     static constexpr int S0 = S0_;                                                         \
     static constexpr bool W = true, FH = FH_, G = true, FH_PAD = PAD_;                     \
     static constexpr bool P1F = true;                                                      \
+    static constexpr int CLUSTER = 0;                                                      \
+  };
+// Cluster form (full first pass shared by a thread-block cluster): C_ CTAs
+// evaluate one cell together; the forward spectrum Fh and two term buffers
+// (double-buffered over the terms) live in the cluster's global workspace, every
+// pass's pencils are split over the CTAs, and CTA r owns S0_ / C_ of the slabs
+// with their gain accumulators in its shared memory for all terms.
+#define COLL_CFG_CLUSTER(N_, T_, V_, S0_, C_)                                              \
+  template <> struct Cfg<N_, T_, V_> {                                                     \
+    static constexpr int S0 = S0_;                                                         \
+    static constexpr bool W = true, FH = false, G = true, FH_PAD = true;                   \
+    static constexpr bool P1F = true;                                                      \
+    static constexpr int CLUSTER = C_;                                                     \
   };
 //        N   T      V  S0  W     Fh     G      Fh padded
 COLL_CFG(16, double, 0,  1, true, true,  true,  true)
@@ -56,10 +70,11 @@ COLL_CFG(32, df,     1,  8, true, false, true,  true)
 COLL_CFG(16, float,  1,  2, true, true,  true,  true)
 COLL_CFG(24, float,  1,  2, true, true,  true,  true)
 COLL_CFG(32, float,  1,  2, true, false, true,  true)
-COLL_CFG(48, float,  1,  8, true, false, true,  true)
+COLL_CFG_CLUSTER(48, float, 1, 12, 4)
 COLL_CFG(64, float,  1,  8, false, false, true, true)
 #undef COLL_CFG
 #undef COLL_CFG_P1F
+#undef COLL_CFG_CLUSTER
 
 constexpr int kThreads = 256;
 
@@ -75,15 +90,22 @@ template <int N, typename T, int V = 0> struct Lay {
   static constexpr size_t FH_BYTES = size_t(N) * N * FH_ROW * 2 * sizeof(T);
   static constexpr size_t G_BYTES = size_t(NS) * N * G_ROW * sizeof(T);    // one slab
   static constexpr size_t round16(size_t b) { return (b + 15) / 16 * 16; }
+  static constexpr int SLABS_PER_CTA = Cf::CLUSTER > 0 ? S0 / Cf::CLUSTER : 1;  // gain slabs in shared memory
   static constexpr size_t SMEM = (Cf::W ? round16(W_BYTES) : 0) + (Cf::FH ? round16(FH_BYTES) : 0) +
-                                 (Cf::G ? round16(G_BYTES) : 0);
+                                 (Cf::G ? SLABS_PER_CTA * round16(G_BYTES) : 0);
   // P1F: the whole term's spectrum after the axis-0 pass and the whole gain accumulator
   static constexpr size_t WG_BYTES = Cf::P1F ? size_t(N) * N * N * 2 * sizeof(T) : 0;
-  static constexpr size_t GG_BYTES = Cf::P1F ? size_t(N) * N * G_ROW * sizeof(T) : 0;
-  static constexpr size_t WS = (Cf::W ? 0 : round16(W_BYTES)) + (Cf::FH ? 0 : round16(FH_BYTES)) +
-                               (Cf::G ? 0 : round16(G_BYTES)) + round16(WG_BYTES) + round16(GG_BYTES);
+  static constexpr size_t GG_BYTES = Cf::P1F && Cf::CLUSTER == 0 ? size_t(N) * N * G_ROW * sizeof(T) : 0;
+  // cluster form: Fh and two term buffers per cluster, counted as C equal shares per CTA
+  static constexpr size_t WS_CLUSTER = round16(FH_BYTES) + 2 * round16(WG_BYTES);
+  static constexpr size_t WS = Cf::CLUSTER > 0
+                                   ? (WS_CLUSTER + Cf::CLUSTER - 1) / Cf::CLUSTER
+                                   : (Cf::W ? 0 : round16(W_BYTES)) + (Cf::FH ? 0 : round16(FH_BYTES)) +
+                                         (Cf::G ? 0 : round16(G_BYTES)) + round16(WG_BYTES) + round16(GG_BYTES);
   static_assert(SMEM <= 232448, "shared-memory layout exceeds 227 KB");
   static_assert(N % S0 == 0, "S0 must divide N");
+  static_assert(Cf::CLUSTER == 0 || (Cf::P1F && Cf::W && Cf::G && !Cf::FH && S0 % Cf::CLUSTER == 0),
+                "the cluster form: full first pass, Fh global, whole slabs per CTA");
 };
 
 }  // namespace coll

@@ -536,6 +536,7 @@ bool mixed_layout(int N, int parts, LayoutInfo* out) {
   i.fh_bytes = size_t(N) * (N / 2) * N * 8;        // forward half spectrum (FP32 complex)
   i.w_bytes = size_t(N) * N * rb;                  // one pass buffer
   i.g_bytes = 0;                                   // the gain accumulator lives in tensor memory
+  i.ws = i.fh_bytes + i.w_bytes;
   *out = i;
   return true;
 }

@@ -725,6 +725,8 @@ bool sliced_layout(int N, LayoutInfo* out) {
   i.fh_bytes = N == 16 ? SlCfg<16>::F_BYTES : SlCfg<32>::F_BYTES;
   i.w_bytes = N == 16 ? SlCfg<16>::BUF_BYTES : SlCfg<32>::BUF_BYTES;
   i.g_bytes = N == 16 ? SlCfg<16>::G_BYTES : SlCfg<32>::G_BYTES;
+  i.smem = N == 16 ? SlCfg<16>::SMEM : SlCfg<32>::SMEM;
+  i.ws = i.fh_bytes + i.w_bytes + i.g_bytes;       // F, the pass buffer and G in global memory
   *out = i;
   return true;
 }
