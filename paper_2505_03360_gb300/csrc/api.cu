@@ -116,6 +116,12 @@ coll_status ragged_prepare(const coll_cell_group* groups, const int64_t* cells, 
     acc += it.n_cells;
   }
   t->total_units = acc;
+  t->smem_bytes = 0;
+  for (int k = 0; k < n; ++k)
+    if (t->items[k].n_cells > 0) {
+      const size_t b = ragged_body_smem(t->items[k].N, *ctype, t->items[k].variant);
+      t->smem_bytes = b > t->smem_bytes ? b : t->smem_bytes;
+    }
   int per = 0;
   if (ragged_max_ctas_per_sm(*ctype, &per) != 0 || per < 1) return COLL_ECUDA;
   size_t smem = 0;

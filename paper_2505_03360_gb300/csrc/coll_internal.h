@@ -103,10 +103,13 @@ struct RaggedTable {
   RaggedItem items[kMaxRaggedGroups];
   int n_items;
   long long total_units;
+  size_t smem_bytes;           // dynamic shared memory of the largest body the launch runs
 };
 // ctype: kCF32 (float io) or kCF64 / kCDF (double io)
 int launch_ragged(int ctype, const RaggedTable& t, void* ws, size_t ws_per_cta, int grid, void* stream);
 int ragged_layout(int ctype, size_t* smem_bytes, size_t* ws_per_cta);
+// shared memory of the body a ragged launch runs for a group of (N, compute type, variant)
+size_t ragged_body_smem(int N, int ctype, int variant);
 int ragged_max_ctas_per_sm(int ctype, int* ctas);
 
 // Mixed-precision (tensor-core DFT-GEMM) collision kernel (mixed.cu)

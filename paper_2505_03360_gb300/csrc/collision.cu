@@ -145,6 +145,31 @@ int ragged_layout(int ctype, size_t* smem_bytes, size_t* ws_per_cta) {
   return int(cudaErrorInvalidValue);
 }
 
+template <int N, typename T> size_t body_smem(int variant) {
+  return variant ? Lay<N, T, RaggedBody<N, T, 1>::v>::SMEM : Lay<N, T, RaggedBody<N, T, 0>::v>::SMEM;
+}
+
+size_t ragged_body_smem(int N, int ctype, int variant) {
+  if (ctype == kCF32) {
+    switch (N) {
+      case 16: return body_smem<16, float>(variant);
+      case 24: return body_smem<24, float>(variant);
+      case 32: return body_smem<32, float>(variant);
+      case 48: return body_smem<48, float>(variant);
+      case 64: return body_smem<64, float>(variant);
+    }
+    return 0;
+  }
+  if (ctype == kCF64 || ctype == kCDF) {
+    switch (N) {
+      case 16: return ctype == kCF64 ? body_smem<16, double>(variant) : body_smem<16, df>(variant);
+      case 24: return ctype == kCF64 ? body_smem<24, double>(variant) : body_smem<24, df>(variant);
+      case 32: return ctype == kCF64 ? body_smem<32, double>(variant) : body_smem<32, df>(variant);
+    }
+  }
+  return 0;
+}
+
 int ragged_max_ctas_per_sm(int ctype, int* ctas) {
   switch (ctype) {
     case kCF32: return ragged_occupancy_f32(ctas);

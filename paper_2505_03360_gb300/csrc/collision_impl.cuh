@@ -379,11 +379,6 @@ __device__ __noinline__ bool ragged_cell(const Tio* f, Tio* Q, const typename C2
   return bad;
 }
 
-// The body a ragged launch runs for variant V of (N, T): the cluster form needs a
-// cluster launch of its own, so its cells take the variant-0 body (the full first
-// pass, whose arithmetic it shares).
-template <int N, typename T, int V> constexpr int kRaggedV = Cfg<N, T, V>::CLUSTER > 0 ? 0 : V;
-
 // per-N body in the slab shape the group's plan uses (so that a ragged launch
 // equals coll_eval_batch of each group alone, whichever shape the autotuner chose)
 template <typename T, typename Tio, int N0, int... Ns>
@@ -391,8 +386,8 @@ struct RaggedDispatch<T, Tio, N0, Ns...> {
   static __device__ __forceinline__ void run(int N, int V, const Tio* f, Tio* Q, const typename C2<T>::type* tab,
                                              int nt, unsigned char* smem, unsigned char* wsc, bool& bad) {
     if (N == N0) {
-      if (V == 1) bad |= ragged_cell<N0, T, Tio, kRaggedV<N0, T, 1>>(f, Q, tab, nt, smem, wsc);
-      else bad |= ragged_cell<N0, T, Tio, 0>(f, Q, tab, nt, smem, wsc);
+      if (V == 1) bad |= ragged_cell<N0, T, Tio, RaggedBody<N0, T, 1>::v>(f, Q, tab, nt, smem, wsc);
+      else bad |= ragged_cell<N0, T, Tio, RaggedBody<N0, T, 0>::v>(f, Q, tab, nt, smem, wsc);
     } else {
       RaggedDispatch<T, Tio, Ns...>::run(N, V, f, Q, tab, nt, smem, wsc, bad);
     }
@@ -431,19 +426,22 @@ template <typename T, typename Tio, int... Ns>
 struct RaggedLaunch {
   static constexpr size_t smem() {      // the largest of every N's two slab shapes
     size_t m = 0;
-    for (size_t v : {Lay<Ns, T, 0>::SMEM..., Lay<Ns, T, kRaggedV<Ns, T, 1>>::SMEM...}) m = v > m ? v : m;
+    for (size_t v : {Lay<Ns, T, RaggedBody<Ns, T, 0>::v>::SMEM..., Lay<Ns, T, RaggedBody<Ns, T, 1>::v>::SMEM...}) m = v > m ? v : m;
     return m;
   }
   static constexpr size_t ws() {        // per CTA: 256-byte header + the largest scratch
     size_t m = 0;
-    for (size_t v : {Lay<Ns, T, 0>::WS..., Lay<Ns, T, kRaggedV<Ns, T, 1>>::WS...}) m = v > m ? v : m;
+    for (size_t v : {Lay<Ns, T, RaggedBody<Ns, T, 0>::v>::WS..., Lay<Ns, T, RaggedBody<Ns, T, 1>::v>::WS...}) m = v > m ? v : m;
     return 256 + (m + 255) / 256 * 256;
   }
+  // dynamic shared memory of the launch: that of the largest body it runs
+  // (t.smem_bytes), not of the largest it could run, so that the L1 keeps the rest
   static int launch(const RaggedTable& t, void* wsp, size_t ws_per_cta, int grid, cudaStream_t st) {
     auto k = ragged_kernel<T, Tio, Ns...>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
     if (e != cudaSuccess) return int(e);
-    k<<<grid, kThreads, smem(), st>>>(t, wsp, ws_per_cta);
+    const size_t sm = t.smem_bytes > 0 && t.smem_bytes <= smem() ? t.smem_bytes : smem();
+    k<<<grid, kThreads, sm, st>>>(t, wsp, ws_per_cta);
     return int(cudaGetLastError());
   }
   static int occupancy(int* ctas) {

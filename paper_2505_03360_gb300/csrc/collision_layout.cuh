@@ -68,15 +68,31 @@ COLL_CFG(16, df,     1,  2, true, true,  true,  true)
 COLL_CFG(24, df,     1,  4, true, true,  true,  true)
 COLL_CFG(32, df,     1,  8, true, false, true,  true)
 COLL_CFG(16, float,  1,  2, true, true,  true,  true)
-COLL_CFG(24, float,  1,  2, true, true,  true,  true)
+COLL_CFG(24, float,  1,  1, true, false, true,  true)
 COLL_CFG(32, float,  1,  2, true, false, true,  true)
 COLL_CFG_CLUSTER(48, float, 1, 12, 4)
 COLL_CFG(64, float,  1,  8, false, false, true, true)
+// bodies of the ragged kernel only (RaggedBody below), not plan variants
+COLL_CFG_P1F(32, float, 2, 4, false, true)
 #undef COLL_CFG
 #undef COLL_CFG_P1F
 #undef COLL_CFG_CLUSTER
 
 constexpr int kThreads = 256;
+
+// The body the ragged kernel (one CTA per cell, one launch for every group) runs
+// for variant V of (N, T): V itself, or a variant with the same arithmetic (equal
+// results bit for bit) that fits that launch better.  The cluster form needs a
+// cluster launch of its own (its cells take the one-CTA full first pass); FP32
+// N = 24 and 32 variants 0 keep Fh in shared memory too (228 and 227 KB), and
+// the ragged launch requests the shared memory of its largest body, so either
+// would leave every other body of the launch the smallest L1 (the N = 48 body,
+// which reads its spectrum and tables through L1, runs 20 % slower): their cells
+// take the same schedule with Fh in global memory (N = 24 variant 1, 173 KB;
+// N = 32 configuration 2, 101 KB).
+template <int N, typename T, int V> struct RaggedBody { static constexpr int v = Cfg<N, T, V>::CLUSTER > 0 ? 0 : V; };
+template <> struct RaggedBody<24, float, 0> { static constexpr int v = 1; };
+template <> struct RaggedBody<32, float, 0> { static constexpr int v = 2; };
 
 template <int N, typename T, int V = 0> struct Lay {
   using Cf = Cfg<N, T, V>;
