@@ -180,13 +180,17 @@ coll_status coll_eval_batch(coll_plan plan, const void* f, void* Q, int64_t n_ce
 /*
  * Autotuner: the fused kernel has two slab shapes per (N, precision) (how
  * many v0-slabs the axis-0 inverse pass is split into, and which arrays stay
- * in shared memory).  coll_plan_autotune times each on the caller's batch
- * (one warm-up and two timed evaluations each, on `stream`; the call
- * synchronises) and stores the faster one in the plan; *chosen (may be NULL)
- * receives it.  Q is overwritten.  ws must hold coll_workspace_size(plan,
- * n_cells) bytes, which covers every shape.  Results of both shapes agree to
- * rounding (the same operations in a different order of slabs).
- * coll_plan_set_variant selects a shape directly (0 or 1).
+ * in shared memory; for FP32 N = 48 the second is the cluster form, four CTAs
+ * per cell).  coll_plan_autotune times each on the caller's batch (one warm-up
+ * and two timed evaluations each, on `stream`; the call synchronises) and
+ * stores the faster one in the plan; *chosen (may be NULL) receives it.  Q is
+ * overwritten.  ws must hold coll_workspace_size(plan, n_cells) bytes, which
+ * covers every shape.  Results of both shapes agree to rounding (the same
+ * operations in a different order of slabs), bit for bit where the shapes
+ * share the schedule (FP32 N = 24, 48).  A new plan starts in shape 0, or in
+ * the cluster form where the (N, precision) has one (faster at every batch
+ * size: more SMs per cell for small batches, the cluster's workspace in L2 for
+ * large ones).  coll_plan_set_variant selects a shape directly (0 or 1).
  */
 coll_status coll_plan_autotune(coll_plan plan, const void* f, void* Q, int64_t n_cells, void* ws,
                                size_t ws_bytes, coll_stream stream, int32_t* chosen);

@@ -29,10 +29,15 @@ bool valid_N(int N, int ctype) {
 
 bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
 
+// CTAs of one launch (the workspace holds one slice per CTA): at most one
+// resident wave and one cell per CTA; a cluster form takes whole clusters of C
+// CTAs (one cell per cluster), at least one
 int grid_for(const coll_plan_s* p, int variant, long long n_cells) {
+  const long long C = p->lay[variant].cluster > 0 ? p->lay[variant].cluster : 1;
   long long g = static_cast<long long>(p->num_sms) * p->ctas_per_sm[variant];
-  if (g > n_cells) g = n_cells;
-  if (g < 1) g = 1;
+  if (g > n_cells * C) g = n_cells * C;
+  g = g / C * C;
+  if (g < C) g = C;
   return int(g);
 }
 
@@ -240,6 +245,7 @@ coll_status coll_plan_create(const coll_plan_desc* desc, coll_plan* out) {
       return COLL_ECUDA;
     }
     p->ctas_per_sm[v] = per;
+    if (p->lay[v].cluster > 0) p->variant = v;        // the cluster form where there is one
   }
 
   const size_t n = ht.tab.size();

@@ -59,13 +59,15 @@ extern "C" coll_status coll_eval_batch_static(coll_plan p, const void* f, void* 
   if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return COLL_EINVAL;
   const int v = p->variant;
   const size_t per_cta = p->lay[v].ws_bytes_per_cta();
+  const long long C = p->lay[v].cluster > 0 ? p->lay[v].cluster : 1;   // CTAs per cell
   long long grid = static_cast<long long>(p->num_sms) * p->ctas_per_sm[v];
-  if (grid > n_cells) grid = n_cells;
+  if (grid > n_cells * C) grid = n_cells * C;
   if (per_cta > 0) {
     const long long fit = static_cast<long long>(kStaticScratchBytes / per_cta);
-    if (fit < 1) return COLL_ENOMEM;            // one CTA's scratch exceeds the fixed array
+    if (fit < C) return COLL_ENOMEM;            // one cell's scratch exceeds the fixed array
     if (grid > fit) grid = fit;                  // fewer resident CTAs, each loops over more cells
   }
+  grid = grid / C * C;                           // whole clusters
   void* ws = nullptr;
   if (scratch_address(dev, &ws) != cudaSuccess) return COLL_ECUDA;
   coll::CollArgs a;
