@@ -492,7 +492,7 @@ def run_ours(args, rank, world, local_rank):
         plan2.close()
         return
     w = WORKLOAD
-    N, n = w["N"], args.cells
+    N, n = (args.N if args.profile_only else w["N"]), args.cells
     f_host = synth.bimodal_batch(n, N, w["L"], seed=synth.BASE_SEED + 2 + 1000 * rank)
     f_pin = torch.from_numpy(f_host).pin_memory()
     f = f_pin.to(dev)
@@ -504,6 +504,8 @@ def run_ours(args, rank, world, local_rank):
     Q = torch.empty_like(f)
     plan = coll.Plan(N, w["L"], lam=w["lam"], M=w["M"], Mtheta=w["Mtheta"], Mr=w["Mr"], prec=prec_main,
                      max_cells=n, device=dev)
+    if args.profile_only and args.variant is not None:
+        coll.coll_plan_set_variant(plan.handle, args.variant)
     ws = plan.reserve(n)
     mom = torch.empty((n, coll.MOMENT_DOUBLES), dtype=torch.float64, device=dev)
     mask = torch.empty((n,), dtype=torch.uint8, device=dev)
@@ -553,8 +555,8 @@ def run_ours(args, rank, world, local_rank):
 
     if args.profile_only:
         if rank == 0:
-            print(json.dumps({"profile_only": True, "cells": n, "ms_per_step": 1e3 * elapsed / args.steps,
-                              "collision_ms": coll_ms}), flush=True)
+            print(json.dumps({"profile_only": True, "N": N, "prec": prec_main, "cells": n,
+                              "ms_per_step": 1e3 * elapsed / args.steps, "collision_ms": coll_ms}), flush=True)
         plan.close()
         return
     # end to end through the C ABI from pinned host buffers: every step uploads its f, evaluates
@@ -1000,6 +1002,10 @@ def main():
     ap.add_argument("--prec", default="f64", choices=["f64", "f32x2", "f32", "mixed_f16x2", "mixed_bf16x3",
                                                       "mixed_sliced"],
                     help="compute precision of the main path in --profile-only runs")
+    ap.add_argument("--N", type=int, default=WORKLOAD["N"],
+                    help="velocity grid N of the main path in --profile-only runs")
+    ap.add_argument("--variant", type=int, default=None, choices=[0, 1],
+                    help="slab shape of the main path's plan in --profile-only runs (default: the plan's own)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
