@@ -70,8 +70,8 @@ typedef enum {
                              leading product levels are summed exactly by the
                              FP32 accumulator, intermediates are float pairs:
                              about 38 significant bits per transform (relative
-                             L2 error ~1e-8 against FP64); N = 16, 32; not in
-                             ragged launches                                   */
+                             L2 error ~1e-8 against FP64); N = 16, 32; in
+                             ragged launches over groups of one N              */
 } coll_precision;
 
 /*
@@ -228,7 +228,11 @@ coll_status coll_eval_batch_static(coll_plan plan, const void* f, void* Q, int64
  * costliest cells start first.  Every plan must live on the current device
  * and use the same compute type, with
  * the io type that goes with it (COLL_F32: float io; COLL_F64 and COLL_F32X2:
- * double io); otherwise COLL_EUNSUPPORTED.  Results are bitwise identical to
+ * double io); otherwise COLL_EUNSUPPORTED.  COLL_MIXED_SLICED groups must also
+ * share N and their io type (one launch of the two-CTA-cluster tensor-core
+ * kernel, cells strided over the clusters); the other tensor-core types have no
+ * ragged launch (COLL_EUNSUPPORTED).  Galerkin plans (dealias = 1) are not
+ * accepted (COLL_EUNSUPPORTED).  Results are bitwise identical to
  * coll_eval_batch of each group alone (same per-cell code and order of
  * operations).  ws (256-byte aligned) must hold coll_ragged_workspace_size()
  * bytes for the same groups; its first 256 bytes hold the work counter, reset

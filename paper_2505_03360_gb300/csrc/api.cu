@@ -86,8 +86,11 @@ coll_status ragged_prepare(const coll_cell_group* groups, const int64_t* cells, 
   const coll_plan_s* p0 = groups[0].plan;
   if (!p0) return COLL_EINVAL;
   *ctype = p0->ctype;
-  if (is_mixed(p0->ctype)) return COLL_EUNSUPPORTED;      // the ragged kernel runs SIMT compute types only
-  const bool want_io_f64 = p0->ctype != kCF32;
+  // SIMT compute types: one persistent kernel over every N; fixed-point slices:
+  // one launch of the sliced kernel over groups of one N; other tensor-core types: none
+  const bool sliced = p0->ctype == kCMixSliced;
+  if (is_mixed(p0->ctype) && !sliced) return COLL_EUNSUPPORTED;
+  const bool want_io_f64 = sliced ? p0->io_f64 : p0->ctype != kCF32;
   int order[kMaxRaggedGroups];
   for (int i = 0; i < n; ++i) {
     const coll_plan_s* p = groups[i].plan;
@@ -95,6 +98,7 @@ coll_status ragged_prepare(const coll_cell_group* groups, const int64_t* cells, 
     if (p->galerkin) return COLL_EUNSUPPORTED;          // ragged launches run N-point products only
     if (p->ctype != *ctype) return COLL_EUNSUPPORTED;
     if (p->io_f64 != want_io_f64) return COLL_EUNSUPPORTED;
+    if (sliced && p->d.N != p0->d.N) return COLL_EUNSUPPORTED;   // the sliced kernel is compiled per N
     if (cells[i] > 0 && (!groups[i].f || !groups[i].Q || groups[i].f == groups[i].Q)) return COLL_EINVAL;
     order[i] = i;
   }
@@ -121,12 +125,22 @@ coll_status ragged_prepare(const coll_cell_group* groups, const int64_t* cells, 
     acc += it.n_cells;
   }
   t->total_units = acc;
+  t->io_f64 = want_io_f64 ? 1 : 0;
   t->smem_bytes = 0;
   for (int k = 0; k < n; ++k)
     if (t->items[k].n_cells > 0) {
       const size_t b = ragged_body_smem(t->items[k].N, *ctype, t->items[k].variant);
       t->smem_bytes = b > t->smem_bytes ? b : t->smem_bytes;
     }
+  if (sliced) {                      // clusters of two CTAs, one cell each, workspace slot per CTA pair
+    *ws_per_cta = p0->lay[0].ws_bytes_per_cta();
+    long long g = static_cast<long long>(p0->num_sms) * p0->ctas_per_sm[0] / 2;
+    if (g > acc) g = acc;
+    if (g < 1) g = 1;
+    *grid = int(2 * g);
+    *total_bytes = 256 + size_t(*grid) * (*ws_per_cta);
+    return COLL_OK;
+  }
   int per = 0;
   if (ragged_max_ctas_per_sm(*ctype, &per) != 0 || per < 1) return COLL_ECUDA;
   size_t smem = 0;

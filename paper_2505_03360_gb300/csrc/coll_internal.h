@@ -104,6 +104,7 @@ struct RaggedTable {
   int n_items;
   long long total_units;
   size_t smem_bytes;           // dynamic shared memory of the largest body the launch runs
+  int io_f64;                  // 1: double f and Q (the fixed-point-slice groups may use either)
 };
 // ctype: kCF32 (float io) or kCF64 / kCDF (double io)
 int launch_ragged(int ctype, const RaggedTable& t, void* ws, size_t ws_per_cta, int grid, void* stream);
@@ -121,6 +122,9 @@ int mixed_set_drop_commit(int on);      // failure injection (coll_debug.h)
 // Fixed-point-slice tensor-core collision kernel (sliced.cu)
 bool sliced_layout(int N, LayoutInfo* out);
 int launch_sliced(int N, bool io_f64, const CollArgs& a, int grid, void* stream);
+// one launch over the cells of several fixed-point-slice plans of one N (a ragged table)
+int launch_sliced_ragged(int N, bool io_f64, const RaggedTable& t, void* ws, size_t ws_per_cta, int grid,
+                         void* stream);
 int sliced_max_ctas_per_sm(int N, bool io_f64, int* ctas);
 
 // Moments kernel (moments.cu)

@@ -132,6 +132,10 @@ int launch_ragged(int ctype, const RaggedTable& t, void* ws, size_t ws_per_cta, 
     case kCF32: return ragged_launch_f32(t, ws, ws_per_cta, grid, st);
     case kCF64: return ragged_launch_f64(t, ws, ws_per_cta, grid, st);
     case kCDF: return ragged_launch_x(t, ws, ws_per_cta, grid, st);
+    case kCMixSliced:                 // slots after the 256-byte head, as for the SIMT kernel
+      return t.n_items > 0 ? launch_sliced_ragged(t.items[0].N, t.io_f64 != 0, t, static_cast<char*>(ws) + 256,
+                                                  ws_per_cta, grid, stream)
+                           : int(cudaErrorInvalidValue);
   }
   return int(cudaErrorInvalidValue);
 }

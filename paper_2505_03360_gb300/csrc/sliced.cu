@@ -590,8 +590,57 @@ struct SlCell {
   }
 };
 
-template <int N, typename Tio>
-__global__ void __launch_bounds__(SlCfg<N>::THREADS, 1) sliced_kernel(CollArgs a) {
+// The cells a launch evaluates: one plan's batch (SlBatch), or the cells of
+// several plans of the same N in table order (SlGroups, a ragged launch: each
+// group has its own f, Q, term tables and status; the DFT matrices depend on N
+// only, so the first group's image serves all).
+template <typename Tio> struct SlCellRef {
+  const Tio* f;
+  Tio* Q;
+  const float4* tab;
+  const float* tmax;
+  int n_terms;
+  int* status;
+};
+template <int N, typename Tio> struct SlBatch {
+  const CollArgs& a;
+  __device__ long long count() const { return a.n_cells; }
+  __device__ const unsigned char* image() const {
+    return static_cast<const unsigned char*>(a.tab) + sliced_img_offset(N, a.n_terms);
+  }
+  __device__ SlCellRef<Tio> cell(long long c) const {
+    const unsigned char* tb = static_cast<const unsigned char*>(a.tab);
+    return {static_cast<const Tio*>(a.f) + size_t(c) * N * N * N, static_cast<Tio*>(a.Q) + size_t(c) * N * N * N,
+            reinterpret_cast<const float4*>(tb), reinterpret_cast<const float*>(tb + sliced_tmax_offset(N, a.n_terms)),
+            a.n_terms, a.status};
+  }
+  __device__ void report_all(int bits) const { atomicOr(a.status, bits); }
+};
+template <int N, typename Tio> struct SlGroups {
+  const RaggedTable& t;
+  __device__ long long count() const { return t.total_units; }
+  __device__ const unsigned char* image() const {
+    return static_cast<const unsigned char*>(t.items[0].tab) + sliced_img_offset(N, t.items[0].n_terms);
+  }
+  __device__ SlCellRef<Tio> cell(long long u) const {
+    int g = 0;
+    while (g + 1 < t.n_items && u >= t.items[g + 1].first_unit) ++g;
+    const RaggedItem& it = t.items[g];
+    const long long c = u - it.first_unit;
+    const unsigned char* tb = static_cast<const unsigned char*>(it.tab);
+    return {static_cast<const Tio*>(it.f) + size_t(c) * N * N * N, static_cast<Tio*>(it.Q) + size_t(c) * N * N * N,
+            reinterpret_cast<const float4*>(tb), reinterpret_cast<const float*>(tb + sliced_tmax_offset(N, it.n_terms)),
+            it.n_terms, it.status};
+  }
+  __device__ void report_all(int bits) const {
+    for (int g = 0; g < t.n_items; ++g) atomicOr(t.items[g].status, bits);
+  }
+};
+
+// Kernel body: one cell per cluster of two CTAs, persistent over the source's
+// cells; each cell's non-finite flag goes to its own plan's status.
+template <int N, typename Tio, typename Src>
+__device__ __forceinline__ void sliced_body(const Src& src, void* wsp, size_t ws_per_cta) {
   using C = SlCfg<N>;
   extern __shared__ __align__(1024) unsigned char smraw[];
   __shared__ SlShared sh;
@@ -603,7 +652,7 @@ __global__ void __launch_bounds__(SlCfg<N>::THREADS, 1) sliced_kernel(CollArgs a
   const uint32_t abase = base + C::B_BYTES + wg * C::A_TILE;
 
   // matrices: copy the pre-swizzled image
-  const unsigned char* img = static_cast<const unsigned char*>(a.tab) + sliced_img_offset(N, a.n_terms);
+  const unsigned char* img = src.image();
   for (int i = tid; i < C::B_BYTES / 16; i += C::THREADS)
     reinterpret_cast<uint4*>(sm)[i] = __ldg(reinterpret_cast<const uint4*>(img) + i);
   if (warp == 0) {
@@ -627,18 +676,16 @@ __global__ void __launch_bounds__(SlCfg<N>::THREADS, 1) sliced_kernel(CollArgs a
   const uint32_t tbase = sh.tbase;
   const uint32_t tacc = tbase + wg * 4 * C::NOUT;
   uint32_t phase = 0;
-  bool pending = false, bad = false;
-  const auto* tab = static_cast<const float4*>(a.tab);
-  const float* tmax = reinterpret_cast<const float*>(static_cast<const unsigned char*>(a.tab) +
-                                                     sliced_tmax_offset(N, a.n_terms));
+  bool pending = false;
   // a cell per cluster of two CTAs; the cluster works in the workspace slot of its first CTA
-  unsigned char* ws = static_cast<unsigned char*>(a.ws) + size_t(blockIdx.x & ~1u) * a.ws_per_cta;
-  for (long long c = blockIdx.x >> 1; c < a.n_cells; c += gridDim.x >> 1) {
-    const Tio* f = static_cast<const Tio*>(a.f) + size_t(c) * N * N * N;
-    Tio* Q = static_cast<Tio*>(a.Q) + size_t(c) * N * N * N;
-    if (SlCell<N, Tio>::cell(f, Q, tab, tmax, a.n_terms, ws, sm + C::B_BYTES + wg * C::A_TILE, abase, bbase, tacc,
-                             phase, pending, sh, bad))
-      break;
+  unsigned char* ws = static_cast<unsigned char*>(wsp) + size_t(blockIdx.x & ~1u) * ws_per_cta;
+  for (long long u = blockIdx.x >> 1; u < src.count(); u += gridDim.x >> 1) {
+    const SlCellRef<Tio> c = src.cell(u);
+    bool bad = false;
+    const bool stop = SlCell<N, Tio>::cell(c.f, c.Q, c.tab, c.tmax, c.n_terms, ws, sm + C::B_BYTES + wg * C::A_TILE,
+                                           abase, bbase, tacc, phase, pending, sh, bad);
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(c.status, kStatusNonFinite);
+    if (stop) break;                       // uniform over the cluster (abort is set in both CTAs)
   }
   // A wait that expired may leave this tile group's last MMA batch in flight.
   // A fresh commit from the issuing thread to a barrier of its own arrives once
@@ -649,8 +696,8 @@ __global__ void __launch_bounds__(SlCfg<N>::THREADS, 1) sliced_kernel(CollArgs a
     (void)wait_parity(&sh.tbar[wg], 0);
   }
   fence_before();
-  if (__syncthreads_or(bad) && tid == 0) atomicOr(a.status, kStatusNonFinite);
-  if (sh.abort && tid == 0) atomicOr(a.status, kStatusTimeout);
+  __syncthreads();
+  if (sh.abort && tid == 0) src.report_all(kStatusTimeout);
   if (warp == 0) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(C::TCOLS));
@@ -658,38 +705,66 @@ __global__ void __launch_bounds__(SlCfg<N>::THREADS, 1) sliced_kernel(CollArgs a
   cluster_sync();                          // no CTA leaves while its peer may still address its shared memory
 }
 
-// Launch in clusters of two CTAs (one cell per cluster).  `grid` is the number
-// of CTAs the caller's workspace covers (a.ws_per_cta each); the kernel uses
-// every other slot, so any grid >= 1 fits: it runs max(1, grid / 2) clusters,
-// capped at the number of clusters that can be resident at once.
 template <int N, typename Tio>
-int launch_sliced_t(const CollArgs& a, int grid, cudaStream_t st) {
+__global__ void __launch_bounds__(SlCfg<N>::THREADS, 1) sliced_kernel(CollArgs a) {
+  sliced_body<N, Tio>(SlBatch<N, Tio>{a}, a.ws, a.ws_per_cta);
+}
+
+template <int N, typename Tio>
+__global__ void __launch_bounds__(SlCfg<N>::THREADS, 1) sliced_ragged_kernel(RaggedTable t, void* ws,
+                                                                             size_t ws_per_cta) {
+  sliced_body<N, Tio>(SlGroups<N, Tio>{t}, ws, ws_per_cta);
+}
+
+template <int N>
+void sl_config(cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr, cudaStream_t st) {
   using C = SlCfg<N>;
-  auto k = sliced_kernel<N, Tio>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-  if (e != cudaSuccess) return int(e);
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 2;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(C::THREADS);
-  cfg.dynamicSmemBytes = C::SMEM;
-  cfg.stream = st;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg->blockDim = dim3(C::THREADS);
+  cfg->dynamicSmemBytes = C::SMEM;
+  cfg->stream = st;
+  cfg->attrs = attr;
+  cfg->numAttrs = 1;
+}
+
+// Launch in clusters of two CTAs (one cell per cluster).  `grid` is the number
+// of CTAs the caller's workspace covers (ws_per_cta each); the kernel uses
+// every other slot, so any grid >= 1 fits: it runs max(1, grid / 2) clusters,
+// capped at the cell count and at the number of clusters that can be resident.
+template <typename K, typename... Args>
+int sl_launch(K k, int smem, long long cells, int grid, cudaLaunchConfig_t* cfg, Args... args) {
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return int(e);
   long long clusters = grid / 2 < 1 ? 1 : grid / 2;
-  if (clusters > a.n_cells) clusters = a.n_cells;
-  cfg.gridDim = dim3(2);
+  if (clusters > cells) clusters = cells;
+  cfg->gridDim = dim3(2);
   int resident = 0;
-  e = cudaOccupancyMaxActiveClusters(&resident, k, &cfg);
+  e = cudaOccupancyMaxActiveClusters(&resident, k, cfg);
   if (e != cudaSuccess) return int(e);
   if (resident >= 1 && clusters > resident) clusters = resident;
-  cfg.gridDim = dim3(unsigned(2 * clusters));
-  e = cudaLaunchKernelEx(&cfg, k, a);
+  cfg->gridDim = dim3(unsigned(2 * clusters));
+  e = cudaLaunchKernelEx(cfg, k, args...);
   if (e != cudaSuccess) return int(e);
   return int(cudaGetLastError());
+}
+
+template <int N, typename Tio>
+int launch_sliced_t(const CollArgs& a, int grid, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  sl_config<N>(&cfg, attr, st);
+  return sl_launch(sliced_kernel<N, Tio>, SlCfg<N>::SMEM, a.n_cells, grid, &cfg, a);
+}
+
+template <int N, typename Tio>
+int launch_sliced_ragged_t(const RaggedTable& t, void* ws, size_t ws_per_cta, int grid, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  sl_config<N>(&cfg, attr, st);
+  return sl_launch(sliced_ragged_kernel<N, Tio>, SlCfg<N>::SMEM, t.total_units, grid, &cfg, t, ws, ws_per_cta);
 }
 
 template <int N, typename Tio>
@@ -735,6 +810,18 @@ int launch_sliced(int N, bool io_f64, const CollArgs& a, int grid, void* stream)
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (N == 16) return io_f64 ? launch_sliced_t<16, double>(a, grid, st) : launch_sliced_t<16, float>(a, grid, st);
   if (N == 32) return io_f64 ? launch_sliced_t<32, double>(a, grid, st) : launch_sliced_t<32, float>(a, grid, st);
+  return int(cudaErrorInvalidValue);
+}
+
+int launch_sliced_ragged(int N, bool io_f64, const RaggedTable& t, void* ws, size_t ws_per_cta, int grid,
+                         void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (N == 16)
+    return io_f64 ? launch_sliced_ragged_t<16, double>(t, ws, ws_per_cta, grid, st)
+                  : launch_sliced_ragged_t<16, float>(t, ws, ws_per_cta, grid, st);
+  if (N == 32)
+    return io_f64 ? launch_sliced_ragged_t<32, double>(t, ws, ws_per_cta, grid, st)
+                  : launch_sliced_ragged_t<32, float>(t, ws, ws_per_cta, grid, st);
   return int(cudaErrorInvalidValue);
 }
 

@@ -8,8 +8,8 @@ iteration evaluates the active requests oldest first, up to a cost budget per
 iteration (at least one request), so that early requests finish early instead
 of every request advancing in lockstep: ONE ragged persistent launch per SIMT
 compute type over the cells of the selected requests (coll_eval_ragged), one
-tensor-core launch per selected mixed-precision request, then
-f <- f + dt Q (coll_advance).  A request leaves after its last evaluation; its
+ragged launch of the fixed-point-slice tensor-core kernel per N over the
+selected mixed-precision requests of that N, then f <- f + dt Q (coll_advance).  A request leaves after its last evaluation; its
 memory returns to the budget and the next waiting requests are admitted.
 Latency is measured from arrival to the completion of the request's last
 evaluation.
@@ -153,7 +153,7 @@ class Service:
                     dt = torch.float64 if prec in ("f32x2", "f64") else torch.float32
                     f = torch.zeros((1, N, N, N), dtype=dt, device=self.device)
                     Q = torch.empty_like(f)
-                    if prec in TENSOR:
+                    if prec in TENSOR and prec != "mixed_sliced":
                         for lane in range(len(self.side)):
                             j = Job(rid=-1, arrival_s=0.0, n_cells=1, N=N, lam=lam, precision=p)
                             pl, ws = self._mix_plan(j, lane)
@@ -213,15 +213,18 @@ class Service:
         return chosen
 
     def _iterate(self, active):
-        """One evaluation of the selected jobs: ragged launch per SIMT compute type,
-        one tensor-core launch per mixed job, then f += dt Q."""
+        """One evaluation of the selected jobs: one ragged launch per SIMT compute
+        type, one ragged launch of the sliced kernel per N for the fixed-point-slice
+        jobs, one launch per job for the other tensor-core types, then f += dt Q."""
         chosen = self._select(active)
         by_kind = collections.defaultdict(list)
         for j in chosen:
-            by_kind[effective_precision(j.precision, j.N)].append(j)
+            prec = effective_precision(j.precision, j.N)
+            by_kind[(prec, j.N) if prec == "mixed_sliced" else prec].append(j)
         side_used = []
-        for prec, jobs in by_kind.items():
-            if prec in TENSOR:
+        for kind, jobs in by_kind.items():
+            prec = kind[0] if isinstance(kind, tuple) else kind
+            if prec in TENSOR and prec != "mixed_sliced":
                 ready = torch_event(self.stream)
                 for i, j in enumerate(jobs):
                     st = self.side[i % len(self.side)]

@@ -192,3 +192,59 @@ def test_ragged_mixed_lambda_cost_order():
         assert np.linalg.norm(got - want) / np.linalg.norm(want) <= TOL["f32"], (N, lam)
     for p in plans:
         p.close()
+
+
+@pytest.mark.parametrize("N,lams,counts,io", [
+    (16, [1.0, 0.0, 1.0], [3, 2, 5], 0),
+    (32, [0.0, 1.0], [2, 3], 1),
+])
+def test_sliced_groups_in_one_launch(N, lams, counts, io):
+    """Fixed-point-slice (tensor-core) plans of one N, hard spheres and Maxwell
+    molecules mixed, in one ragged launch of the sliced kernel: every group
+    equals its own coll_eval_batch bit for bit (the per-cell code and pass
+    scales do not depend on the launch), its status is its own, and a sampled
+    cell of each group is within 1e-6 of the oracle."""
+    dt = torch.float64 if io == 0 else torch.float32
+    r = synth.rng(900 + N)
+    plans, fs, Qs = [], [], []
+    for lam, n in zip(lams, counts):
+        Mr = 8
+        plans.append(coll.Plan(N, L, lam=lam, M=32 if N == 16 else 48, Mtheta=4, Mr=Mr, prec="mixed_sliced",
+                               io_dtype=io, max_cells=n))
+        cells = np.stack([synth.anisotropic_cell(N, L, r, dtype=np.float64) for _ in range(n)])
+        fs.append(torch.from_numpy(cells).to("cuda", dt))
+        Qs.append(torch.full_like(fs[-1], float("nan")))
+    groups = [(p.handle, f, Q) for p, f, Q in zip(plans, fs, Qs)]
+    ws = torch.empty(coll.coll_ragged_workspace_size(groups, counts), dtype=torch.uint8, device="cuda")
+    coll.coll_eval_ragged(groups, counts, ws)
+    torch.cuda.synchronize()
+    for p, f, Q, lam, n in zip(plans, fs, Qs, lams, counts):
+        assert p.status() == coll.COLL_OK
+        ref = p.eval(f)
+        torch.cuda.synchronize()
+        assert torch.equal(Q, ref), (lam, n)
+        pr = Params(N=N, L=L, lam=lam, M=32 if N == 16 else 48, Mtheta=4, Mr=8)
+        want = q_fast(f[n - 1].double().cpu().numpy(), pr, multipliers(pr))
+        got = Q[n - 1].double().cpu().numpy()
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) <= 1e-6, (lam, n)
+    for p in plans:
+        p.close()
+
+
+def test_sliced_groups_errors():
+    """A sliced ragged launch takes groups of one N; the other tensor-core types
+    have no ragged launch."""
+    ps16 = coll.Plan(16, L, lam=1.0, M=32, Mtheta=4, Mr=8, prec="mixed_sliced", max_cells=1)
+    ps32 = coll.Plan(32, L, lam=1.0, M=48, Mtheta=4, Mr=8, prec="mixed_sliced", max_cells=1)
+    pf16 = coll.Plan(16, L, lam=1.0, M=32, Mtheta=4, Mr=8, prec="mixed_f16x2", max_cells=1)
+    a = torch.zeros((1, 16, 16, 16), dtype=torch.float64, device="cuda")
+    b = torch.zeros((1, 32, 32, 32), dtype=torch.float64, device="cuda")
+    with pytest.raises(coll.CollError) as e:                   # two N in one sliced launch
+        coll.coll_ragged_workspace_size([(ps16.handle, a, torch.empty_like(a)),
+                                         (ps32.handle, b, torch.empty_like(b))], [1, 1])
+    assert e.value.status == coll.COLL_EUNSUPPORTED
+    with pytest.raises(coll.CollError) as e:                   # f16 hi+lo: no ragged launch
+        coll.coll_ragged_workspace_size([(pf16.handle, a, torch.empty_like(a))], [1])
+    assert e.value.status == coll.COLL_EUNSUPPORTED
+    for p in (ps16, ps32, pf16):
+        p.close()
