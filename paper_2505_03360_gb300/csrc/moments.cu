@@ -311,17 +311,39 @@ template <> struct Bits<float> {
   }
 };
 
+// 16-byte load through the read-only path with an L2 eviction priority: kL2Keep
+// (evict_last) where a later pass reads the cell again, kL2Drop (evict_first)
+// on its last read, so that the lines of finished cells leave L2 before those of
+// cells still in flight.
+enum : int { kL2Normal = 0, kL2Keep = 1, kL2Drop = 2 };
+template <int H>
+__device__ __forceinline__ uint4 ldg_l2(const uint4* p) {
+  uint4 v;
+  if constexpr (H == kL2Normal) {
+    v = __ldg(p);
+  } else {
+    unsigned long long pol;
+    if constexpr (H == kL2Keep)
+      asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    else
+      asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p), "l"(pol));
+  }
+  return v;
+}
+
 // 8 consecutive elements of a row as bit patterns (two 16-byte loads)
-template <typename Tio>
+template <typename Tio, int H = kL2Normal>
 __device__ __forceinline__ void load8(const Tio* p, typename Bits<Tio>::U* b) {
   const uint4* q = reinterpret_cast<const uint4*>(p);
-  const uint4 a = __ldg(q), c = __ldg(q + 1);
+  const uint4 a = ldg_l2<H>(q), c = ldg_l2<H>(q + 1);
   if constexpr (sizeof(Tio) == 8) {
     b[0] = (unsigned long long)a.x | ((unsigned long long)a.y << 32);
     b[1] = (unsigned long long)a.z | ((unsigned long long)a.w << 32);
     b[2] = (unsigned long long)c.x | ((unsigned long long)c.y << 32);
     b[3] = (unsigned long long)c.z | ((unsigned long long)c.w << 32);
-    const uint4 d = __ldg(q + 2), e = __ldg(q + 3);
+    const uint4 d = ldg_l2<H>(q + 2), e = ldg_l2<H>(q + 3);
     b[4] = (unsigned long long)d.x | ((unsigned long long)d.y << 32);
     b[5] = (unsigned long long)d.z | ((unsigned long long)d.w << 32);
     b[6] = (unsigned long long)e.x | ((unsigned long long)e.y << 32);
@@ -659,7 +681,7 @@ __device__ void sums_cell_fast(const Tio* __restrict__ f, double L, unsigned lon
   bool bad = false;
   const uint4* f4 = reinterpret_cast<const uint4*>(f);
   for (int i = tid; i < n3 / VEC; i += kMThreads) {
-    const uint4 v = __ldg(f4 + i);
+    const uint4 v = ldg_l2<kL2Keep>(f4 + i);
     U e[VEC];
     if constexpr (sizeof(Tio) == 8) {
       e[0] = (unsigned long long)v.x | ((unsigned long long)v.y << 32);
@@ -700,7 +722,7 @@ __device__ void sums_cell_fast(const Tio* __restrict__ f, double L, unsigned lon
 #pragma unroll
     for (int c0 = 0; c0 < N; c0 += 8) {
       U b[8];
-      load8<Tio>(fr + c0, b);
+      load8<Tio, kL2Keep>(fr + c0, b);
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int k2 = c0 + e - half;                 // compile-time after unrolling
@@ -735,7 +757,7 @@ __device__ void sums_cell_fast(const Tio* __restrict__ f, double L, unsigned lon
 #pragma unroll
     for (int c0 = 0; c0 < N; c0 += 8) {
       U b[8];
-      load8<Tio>(fr + c0, b);
+      load8<Tio, kL2Drop>(fr + c0, b);
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int F2 = B::fix32(b[e], P2);
@@ -828,7 +850,7 @@ struct ConsShared {
   unsigned int wbad[kMThreads / 32];
 };
 
-// rows [row0, row0 + nrows) of a cell at base (shared or global memory)
+// rows [row0, row0 + nrows) of a cell at base (global memory; the cell's last read)
 template <int N, typename Tio>
 __device__ __forceinline__ void cons_rows(const unsigned char* base, int row0, int nrows, int P, bool general,
                                           i128 (&acc)[8]) {
@@ -861,7 +883,7 @@ __device__ __forceinline__ void cons_rows(const unsigned char* base, int row0, i
         int j = i + s;
         if (j >= NCH) j -= NCH;
         U b[EPC];
-        unpack16<Tio>(*reinterpret_cast<const uint4*>(rp + 16 * j), b);
+        unpack16<Tio>(ldg_l2<kL2Drop>(reinterpret_cast<const uint4*>(rp + 16 * j)), b);
 #pragma unroll
         for (int e = 0; e < EPC; ++e) add(B::fix(b[e], P), j * EPC + e - half);
       }
@@ -916,7 +938,7 @@ __global__ void __launch_bounds__(kMThreads, 4) cons_kernel(const Tio* __restric
     const uint4* s4 = reinterpret_cast<const uint4*>(base);
     for (int i = tid; i < BYTES / 16; i += kMThreads) {
       U e[EPC];
-      unpack16<Tio>(__ldg(s4 + i), e);
+      unpack16<Tio>(ldg_l2<kL2Keep>(s4 + i), e);
 #pragma unroll
       for (int k = 0; k < EPC; ++k) {
         const U a = e[k] & B::kAbs;
