@@ -48,6 +48,33 @@ __device__ __forceinline__ bool finite_v(double x) { return ::isfinite(x); }
 __device__ __forceinline__ bool finite_v(float x) { return ::isfinite(x); }
 __device__ __forceinline__ bool finite_v(df x) { return isfinite(x); }
 
+// The term tables are read by every CTA for every cell and are read-only for
+// the kernel's lifetime.  At N >= 48, where the per-CTA workspaces exceed L2,
+// their loads carry an L2 evict_last policy so that the tables stay (measured
+// 2.5-3 % faster at N = 48 and 64; at N = 32, where the workspaces fit, plain
+// loads are as fast or faster).  A hint only: the values are those of plain loads.
+template <int N> constexpr bool kKeepTables = N >= 48;
+__device__ __forceinline__ unsigned long long l2_keep() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// read-only (non-coherent path) global load of an 8- or 16-byte table element under an L2 policy
+template <typename V>
+__device__ __forceinline__ V ldg_pol(const V* p, unsigned long long pol) {
+  static_assert(sizeof(V) == 8 || sizeof(V) == 16, "complex element of 8 or 16 bytes");
+  if constexpr (sizeof(V) == 8) {
+    union { uint2 u; V v; } r;
+    asm("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(r.u.x), "=r"(r.u.y) : "l"(p), "l"(pol));
+    return r.v;
+  } else {
+    union { uint4 u; V v; } r;
+    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(r.u.x), "=r"(r.u.y), "=r"(r.u.z), "=r"(r.u.w) : "l"(p), "l"(pol));
+    return r.v;
+  }
+}
+
 enum PassMode : int { kPassF1 = 0, kPassFwd = 1, kPassInv = 2, kPassP3 = 3 };
 
 // One pass of length-N register FFTs over a set of pencils (this thread's: p0,
@@ -146,6 +173,7 @@ __device__ __noinline__ void run_p1(const typename C2<T>::type* __restrict__ tb,
   using Ly = Lay<N, T, V>;
   using V2 = typename C2<T>::type;
   constexpr int H = Ly::H, FR = Ly::FH_ROW, WR = Ly::W_ROW, S0 = Ly::S0, NS = Ly::NS;
+  const unsigned long long keep = l2_keep();
   for (int pid = threadIdx.x; pid < N * N; pid += kThreads) {
     const int k1 = pid / N, k2 = pid % N;
     T yr[NS], yi[NS];
@@ -165,7 +193,9 @@ __device__ __noinline__ void run_p1(const typename C2<T>::type* __restrict__ tb,
           const int k0s = up ? (N - k0) % N : k0;
           const size_t idx = (size_t(k0s) * N + k1s);
           const V2 F = Fh[idx * FR + k2s];
-          const V2 AB = tb[idx * H + k2s];
+          V2 AB;
+          if constexpr (kKeepTables<N>) AB = ldg_pol(tb + idx * H + k2s, keep);
+          else AB = tb[idx * H + k2s];
           const T fr = F.x, fi = up ? -F.y : F.y;   // conj for the Hermitian partner
           T xr = AB.x * fr - AB.y * fi;
           T xi = AB.x * fi + AB.y * fr;
@@ -213,6 +243,7 @@ __device__ __noinline__ void run_p1f(const typename C2<T>::type* __restrict__ tb
   using Ly = Lay<N, T, V>;
   using V2 = typename C2<T>::type;
   constexpr int H = Ly::H, FR = Ly::FH_ROW;
+  const unsigned long long keep = l2_keep();
   for (int pid = p0 < 0 ? int(threadIdx.x) : p0; pid < N * N; pid += pstep) {
     const int k1 = pid / N, k2 = pid % N;
     T xr[N], xi[N];
@@ -228,7 +259,9 @@ __device__ __noinline__ void run_p1f(const typename C2<T>::type* __restrict__ tb
         const int k0s = up ? (N - k0) % N : k0;
         const size_t idx = (size_t(k0s) * N + k1s);
         const V2 F = Fh[idx * FR + k2s];
-        const V2 AB = tb[idx * H + k2s];
+        V2 AB;
+        if constexpr (kKeepTables<N>) AB = ldg_pol(tb + idx * H + k2s, keep);
+        else AB = tb[idx * H + k2s];
         const T fr = F.x, fi = up ? -F.y : F.y;   // conj for the Hermitian partner
         xr[k0] = AB.x * fr - AB.y * fi;
         xi[k0] = AB.x * fi + AB.y * fr;
@@ -257,6 +290,7 @@ template <typename V2> __device__ __forceinline__ void cp_elem(V2* dst_smem, con
   if constexpr (sizeof(V2) == 16) cp16(dst_smem, src); else cp8(dst_smem, src);
 }
 __device__ __forceinline__ void cp16_wait() { asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory"); }
+
 
 // ------------------------------------------------------------ per-cell body
 // smem: dynamic shared memory base; wsc: this CTA's workspace slice.
