@@ -563,7 +563,9 @@ def run_ours(args, rank, world, local_rank):
     # Q and the moments/mask, and downloads Q, the records and the mask.  Two buffer sets and
     # three streams (upload, compute, download) overlap step k+1's upload and step k-1's
     # download with step k's compute.
-    e2e_steps = max(3, min(args.steps, 4))
+    # eight steps (fewer if --steps is smaller, at least three): the first upload and the
+    # last download are not overlapped, and the host copy bandwidth differs from box to box
+    e2e_steps = max(3, min(args.steps, 8))
     fb, Qb = [f, torch.empty_like(f)], [Q, torch.empty_like(Q)]
     momb, maskb = [mom, torch.empty_like(mom)], [mask, torch.empty_like(mask)]
     consb = [cons, torch.empty_like(cons)]
