@@ -248,3 +248,71 @@ def test_sliced_groups_errors():
     assert e.value.status == coll.COLL_EUNSUPPORTED
     for p in (ps16, ps32, pf16):
         p.close()
+
+
+def test_ragged_low_rank_maxwell_molecules_with_hard_spheres():
+    """A low-rank Maxwell-molecule plan (rank 5 of Mr = 8 radial nodes, 16 x 5 + 1
+    terms) and hard-sphere plans of other N in one FP32 ragged launch: each group
+    equals its own launch bit for bit, and the low-rank group's sampled cell is
+    within the FP32 tolerance of the oracle's low-rank operator."""
+    from oracle.collision import q_fast_streaming
+    r = synth.rng(4711)
+    specs = [(32, 0.0, 5, 3), (16, 1.0, 0, 5), (24, 1.0, 0, 2)]      # (N, lambda, rank, cells)
+    plans, fs, Qs, cells = [], [], [], []
+    for N, lam, rank, n in specs:
+        plans.append(coll.Plan(N, L, lam=lam, M=32, Mtheta=4, Mr=8, prec="f32", max_cells=n, rank=rank))
+        fs.append(torch.from_numpy(np.stack([synth.anisotropic_cell(N, L, r, dtype=np.float64) for _ in range(n)]))
+                  .to("cuda", torch.float32))
+        Qs.append(torch.full_like(fs[-1], float("nan")))
+        cells.append(n)
+    assert plans[0].n_terms == 16 * 5 + 1
+    groups = [(p.handle, f, Q) for p, f, Q in zip(plans, fs, Qs)]
+    ws = torch.empty(coll.coll_ragged_workspace_size(groups, cells), dtype=torch.uint8, device="cuda")
+    coll.coll_eval_ragged(groups, cells, ws)
+    torch.cuda.synchronize()
+    for p, f, Q in zip(plans, fs, Qs):
+        assert p.status() == coll.COLL_OK
+        ref = p.eval(f)
+        torch.cuda.synchronize()
+        assert torch.equal(Q, ref)
+    pr = Params(N=32, L=L, lam=0.0, M=32, Mtheta=4, Mr=8, rank=5)
+    want = q_fast_streaming(fs[0][2].double().cpu().numpy(), pr)
+    got = Qs[0][2].double().cpu().numpy()
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) <= TOL["f32"]
+    for p in plans:
+        p.close()
+
+
+def test_sliced_groups_cuda_graph_replay():
+    """The grouped tensor-core launch (two fixed-point-slice plans of N = 16)
+    captured in a CUDA graph with its workspace reset: two replays equal the eager
+    launch bit for bit."""
+    r = synth.rng(4712)
+    plans, fs, Qs, cells = [], [], [], [2, 3]
+    for lam, n in zip((1.0, 0.0), cells):
+        plans.append(coll.Plan(16, L, lam=lam, M=32, Mtheta=4, Mr=8, prec="mixed_sliced", max_cells=n))
+        fs.append(torch.from_numpy(np.stack([synth.anisotropic_cell(16, L, r, dtype=np.float64)
+                                             for _ in range(n)])).to("cuda"))
+        Qs.append(torch.full_like(fs[-1], float("nan")))
+    groups = [(p.handle, f, Q) for p, f, Q in zip(plans, fs, Qs)]
+    ws = torch.empty(coll.coll_ragged_workspace_size(groups, cells), dtype=torch.uint8, device="cuda")
+    coll.coll_eval_ragged(groups, cells, ws)
+    torch.cuda.synchronize()
+    eager = [Q.clone() for Q in Qs]
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            coll.coll_eval_ragged(groups, cells, ws, stream=s)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        for Q in Qs:
+            Q.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        for p, Q, E in zip(plans, Qs, eager):
+            assert p.status() == coll.COLL_OK
+            assert torch.equal(Q, E)
+    for p in plans:
+        p.close()
