@@ -89,3 +89,41 @@ def test_galerkin_workspace_and_unsupported_calls():
         coll.coll_ragged_workspace_size([(plan.handle, f, Q)], [n])
     assert e.value.status == coll.COLL_EUNSUPPORTED
     plan.close()
+
+
+def test_galerkin_with_low_rank_radial_kernel():
+    """Both options at once, FP64: Maxwell molecules at rank 5 of Mr = 8 radial
+    nodes with the products on the 3N/2 grid, against the oracle's operator with
+    the same two options (1e-12), mass exact."""
+    N = 16
+    cells = synth.bimodal_batch(2, N, L, seed=synth.BASE_SEED + 130)
+    plan = coll.Plan(N, L, lam=0.0, M=32, Mtheta=4, Mr=8, prec="f64", max_cells=2, dealias=1, rank=5)
+    assert plan.n_terms == 16 * 5 + 1
+    Q = plan.eval(torch.from_numpy(cells).cuda())
+    torch.cuda.synchronize()
+    assert plan.status() == coll.COLL_OK
+    Qg = Q.cpu().numpy()
+    plan.close()
+    p = Params(N=N, L=L, lam=0.0, M=32, Mtheta=4, Mr=8, dealias=1, rank=5)
+    m = multipliers(p)
+    for c in range(len(cells)):
+        want = q_fast(cells[c], p, m)
+        assert rel(Qg[c], want) <= 1e-12, (c, rel(Qg[c], want))
+        assert oc.relative_errors(oc.cell_invariants(Qg[c], L))[0][0] <= 1e-13
+
+
+def test_galerkin_fp32_padded_grid_shapes_agree():
+    """FP32 N = 32 in Galerkin mode runs the N = 48 kernel; its one-CTA shape and
+    its cluster form (the default) give the same result bit for bit."""
+    N = 32
+    cells = synth.bimodal_batch(3, N, L, seed=synth.BASE_SEED + 131).astype(np.float32)
+    plan = coll.Plan(N, L, lam=1.0, M=48, Mtheta=4, Mr=16, prec="f32", max_cells=3, dealias=1)
+    f = torch.from_numpy(cells).cuda()
+    out = []
+    for v in (0, 1):
+        coll.coll_plan_set_variant(plan.handle, v)
+        out.append(plan.eval(f))
+    torch.cuda.synchronize()
+    assert plan.status() == coll.COLL_OK
+    assert torch.equal(out[0], out[1])
+    plan.close()
