@@ -147,3 +147,29 @@ def test_l1_threshold_one_unit_either_side_bit_exact():
             _, gm = check(f[c:c + 1], L, delta0=delta0)
             assert int(gm[0]) & 4 == want, (c, delta0, l1)
 
+
+
+def test_fp64_input_other_sizes():
+    """FP64 cells at every compiled grid size besides N = 32."""
+    for N in (16, 24, 48, 64):
+        check(synth.bimodal_batch(2, N, synth.DEFAULT_L, seed=500 + N), synth.DEFAULT_L)
+
+
+def test_general_kernel_unaligned_input_and_uncompiled_grid():
+    """The general kernel: f not on a 16-byte boundary (a view starting one
+    double into a buffer), and a grid size without a compiled fast path (N = 20);
+    the records are the oracle's, bitwise as everywhere else."""
+    L, N, n = synth.DEFAULT_L, 16, 2
+    f = synth.bimodal_batch(n, N, L, seed=600)
+    buf = torch.empty(n * N ** 3 + 1, dtype=torch.float64, device="cuda")
+    buf[1:] = torch.from_numpy(f).reshape(-1).cuda()
+    fd = buf[1:].view(n, N, N, N)
+    assert fd.data_ptr() % 16 == 8
+    mom, mask = coll.moments(fd, L, 1e-3, 1e-4)
+    torch.cuda.synchronize()
+    r, rm = om.batch(f, L, 1e-3, 1e-4)
+    g, gm = mom.cpu().numpy(), mask.cpu().numpy()
+    assert np.array_equal(gm, rm)
+    np.testing.assert_array_equal(g[:, EXACT], r[:, EXACT])
+    np.testing.assert_allclose(g[:, EIG], r[:, EIG], atol=1e-12, rtol=0)
+    check(synth.bimodal_batch(2, 20, L, seed=601), L)
