@@ -8,6 +8,7 @@ import dataclasses
 import math
 
 import numpy as np
+import pytest
 from scipy import integrate
 
 from oracle import conservation as oc
@@ -22,9 +23,11 @@ def _cells(N, n=2, seed=7):
     return synth.bimodal_batch(n, N, L, seed=seed)
 
 
-def test_full_rank_equals_node_terms():
-    """rank = Mr: U U^T = I, so the rotated terms reproduce the node terms."""
-    p0 = Params(N=16, L=L, lam=0.0, M=32, Mtheta=4, Mr=8)
+@pytest.mark.parametrize("dealias", [0, 1])
+def test_full_rank_equals_node_terms(dealias):
+    """rank = Mr: U U^T = I, so the rotated terms reproduce the node terms, with
+    circular products and with the products on the 3N/2 grid alike."""
+    p0 = Params(N=16, L=L, lam=0.0, M=32, Mtheta=4, Mr=8, dealias=dealias)
     p8 = dataclasses.replace(p0, rank=8)
     f = _cells(16)
     m0, m8 = multipliers(p0), multipliers(p8)
